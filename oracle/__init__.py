@@ -1,0 +1,20 @@
+"""Plain FP64 CPU oracle for boundary-MPS row absorption with rSVD compression.
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path imports, calls or links
+this package: only the tests, ``__graft_entry__.smoke()`` (which checks one
+small GPU run against it) and the CPU-baseline leg of ``bench.py`` use it.
+
+It restates, slowly and in double precision, what the GPU path computes:
+
+* ``philox``   - the Philox4x64-10 counter-based generator and the Box-Muller
+                 Gaussian sketch Omega (paper Sec. IV: Omega is Gaussian).
+* ``network``  - the PEPS-PEPO-PEPS sandwich (Sec. II, Fig. 1), brute-force
+                 state vectors for small lattices and an independent exact
+                 column-wise contraction.
+* ``boundary`` - the boundary-MPS environment approximation (Sec. II) with
+                 rSVD compression (Sec. IV, Halko et al. Example 1.6) and the
+                 CBE variational fit whose A*Omega follows Fig. 5.
+
+It shares no code with the CUDA path; the only common module is the seeded
+input generator ``synth`` (data, no method arithmetic).
+"""
