@@ -1,0 +1,191 @@
+/*
+ * fpeps.h - C ABI of the GB300 boundary-MPS row-absorption library.
+ *
+ * What it computes (Scheb, "Improved contraction of finite projected entangled
+ * pair states", arXiv:2511.01039):
+ *   Sec. II   <psi|O|psi> of an open Lx x Ly PEPS (bond D, physical dim p) with a
+ *             PEPO O (bond w), contracted row by row into a boundary MPS whose
+ *             bundles of D*w*D legs are compressed to a bond chi.
+ *   Sec. III  every compression step is built from the contraction pattern of
+ *             Fig. 2(a): environment, boundary, and the sandwich C of a PEPS, a
+ *             PEPO and the adjoint PEPS tensor (PEPO indices kept separate).
+ *   Sec. IV   the compression uses a randomized SVD (Gaussian sketch, repeated
+ *             application of the matrix and its transpose, thin QR, SVD of the
+ *             projected matrix), first in a left-to-right zip-up pass and then in
+ *             a right-to-left variational fit with controlled bond expansion
+ *             (CBE, Fig. 3-5).
+ *
+ * Conventions
+ *   PEPS site  A[l,u,r,d,p]       PEPO site W[l,u,r,d,p,p']  (p meets the ket,
+ *   p' the bra); open-boundary legs have dimension 1; the bra is A itself (real
+ *   data). Sites are packed in row-major site order (r = 0..Lx-1 top to bottom,
+ *   c = 0..Ly-1 left to right), each site C-contiguous.
+ *   Boundary MPS tensors T_c[t_{c-1}, (u,u_w,u'), t_c], bundle index bra-fastest.
+ *
+ * Threading and streams: an env is not thread-safe; different envs are
+ * independent. All GPU work is enqueued on the stream given at creation.
+ * Calls that return scalars to host memory synchronise that stream; the
+ * others only enqueue work (they may synchronise to read tiny status words).
+ *
+ * Errors: every call returns an fpeps_status; nothing throws, aborts or traps.
+ * After FPEPS_ERR_CUDA the env is poisoned: every later call except
+ * fpeps_last_error and fpeps_env_destroy returns FPEPS_ERR_STATE.
+ */
+#ifndef FPEPS_H
+#define FPEPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FPEPS_OK = 0,
+  FPEPS_ERR_ARG = 1,         /* bad argument (NULL, size, dimension, enum) */
+  FPEPS_ERR_STATE = 2,       /* call out of order, or env poisoned */
+  FPEPS_ERR_OOM = 3,         /* allocator returned NULL */
+  FPEPS_ERR_CUDA = 4,        /* a CUDA call failed; env poisoned */
+  FPEPS_ERR_NUMERIC = 5,     /* non-finite value or failed factorisation */
+  FPEPS_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  FPEPS_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} fpeps_status;
+
+/* Arithmetic of the contraction GEMMs (the QR and the small SVD always run in
+ * FP64-class precision). FP64: everything in double. F32: plain FP32 CUDA-core
+ * products. TF32X3 / BF16X3: split-precision products on the tensor cores,
+ * a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with FP32 accumulation. */
+typedef enum { FPEPS_F64 = 0, FPEPS_F32 = 1, FPEPS_TF32X3 = 2, FPEPS_BF16X3 = 3 } fpeps_precision;
+
+/* Device-memory provider. alloc(ctx, bytes, stream) returns device memory usable
+ * on `stream` (NULL on failure); free(ctx, ptr, stream) releases it. Pass NULL
+ * for the allocator to use cudaMallocAsync/cudaFreeAsync on the env stream. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, void* stream);
+} fpeps_allocator;
+
+typedef struct {
+  int32_t Lx, Ly;        /* lattice, >= 1 */
+  int32_t D;             /* PEPS bond dimension (interior legs), >= 1 */
+  int32_t p;             /* physical dimension, >= 1 */
+  int32_t w;             /* PEPO bond dimension (interior legs), >= 1 */
+  int32_t chi;           /* boundary bond dimension, >= 1 */
+  fpeps_precision prec;  /* contraction arithmetic */
+  uint64_t seed;         /* key of the Gaussian sketches */
+  int32_t symmetry;      /* 0 = dense (1 = U(1)xU(1) block-sparse: not built) */
+  int32_t n_envs;        /* 1 (batched environments: not built) */
+} fpeps_config;
+
+/* rSVD / CBE settings (Sec. IV). Zero-initialised fields take the defaults in
+ * brackets where stated. */
+typedef struct {
+  int32_t oversample;   /* sketch width = kept bond + oversample            */
+  int32_t power_iters;  /* q: applications of A^T A after the first A       */
+  int32_t chi_tilde;    /* CBE expansion width; 0 => ceil(chi / 10)         */
+  int32_t n_fit;        /* 0 = zip-up only, 1 = zip-up + one CBE fit pass   */
+  int32_t exact_svd;    /* 1 => sketch width = full rank (exact factorisation) */
+} fpeps_rsvd_params;
+
+typedef struct {
+  double seconds;        /* device time of the call (CUDA events)         */
+  double alg_flops;      /* algorithmic flops of the contractions          */
+  double log_scale;      /* ln of the scale moved out of the new boundary  */
+  double trunc_err_est;  /* sum of squared discarded Ritz values / total (zip-up) */
+} fpeps_stats;
+
+typedef struct fpeps_env fpeps_env;
+
+/* Create an environment for one PEPS and one operator PEPO.
+ *   cfg        lattice and method configuration (copied).
+ *   peps_dev   device buffer with all PEPS sites (row-major site order, each
+ *              [Dl,Du,Dr,Dd,p] C-contiguous, edge legs 1), element type dtype_in.
+ *   pepo_dev   device buffer with all operator PEPO sites [wl,wu,wr,wd,p,p'],
+ *              or NULL for none (then only fpeps_contract_norm is available).
+ *   charges_host  must be NULL (block-sparse mode is not built).
+ *   dtype_in   0 = float64, 1 = float32.
+ *   cuda_stream   cudaStream_t on which all work is enqueued (NULL = default).
+ *   alloc      device allocator or NULL.
+ * The inputs are copied (and converted to the compute precision) before the
+ * call returns; the caller keeps ownership of its buffers.
+ * Errors: FPEPS_ERR_ARG (bad sizes/pointers), FPEPS_ERR_OOM, FPEPS_ERR_CUDA,
+ * FPEPS_ERR_UNSUPPORTED (symmetry != 0 or n_envs != 1). */
+fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, const void* pepo_dev,
+                              const int32_t* charges_host, int32_t dtype_in, void* cuda_stream,
+                              const fpeps_allocator* alloc, fpeps_env** out);
+
+/* Absorb row `row` (rows must come in order 0, 1, ..., Lx-1; row 0 starts a new
+ * sweep of the given layer). layer 0 = identity PEPO (norm), 1 = operator PEPO.
+ *   row 0        builds the exact boundary from the row-0 sandwiches (Sec. II).
+ *   0<row<Lx-1   stages the row; fpeps_compress_rsvd must follow.
+ *   row Lx-1     closes the network exactly (vector transfer); the sweep value
+ *                becomes available to fpeps_sweep_value.
+ * Errors: FPEPS_ERR_STATE (out of order / compress pending), FPEPS_ERR_ARG. */
+fpeps_status fpeps_absorb_row(fpeps_env* env, int32_t row, int32_t layer);
+
+/* Compress the staged row into a new boundary of bond chi: zip-up rSVD pass,
+ * then n_fit CBE fit passes (Sec. IV). out_host (nullable) receives stats.
+ * Errors: FPEPS_ERR_STATE if no interior row is staged, FPEPS_ERR_NUMERIC if a
+ * factorisation broke down or a value became non-finite. */
+fpeps_status fpeps_compress_rsvd(fpeps_env* env, const fpeps_rsvd_params* params, fpeps_stats* out_host);
+
+/* Value of the sweep closed by the last absorbed row: sign and ln|value|. */
+fpeps_status fpeps_sweep_value(fpeps_env* env, double* log_abs, int32_t* sign);
+
+/* Full sweep with the identity PEPO: <psi|psi> = sign * exp(log_abs). */
+fpeps_status fpeps_contract_norm(fpeps_env* env, const fpeps_rsvd_params* params, double* log_abs,
+                                 int32_t* sign);
+
+/* Full sweeps with the operator PEPO (layer 1) and the identity (layer 0):
+ * value = <psi|O|psi> / <psi|psi>; the numerator as (sign_num, log_abs_num).
+ * Errors: FPEPS_ERR_STATE if the env has no operator PEPO. */
+fpeps_status fpeps_expect(fpeps_env* env, const fpeps_rsvd_params* params, double* value,
+                          double* log_abs_num, int32_t* sign_num);
+
+/* Checkpoint of the current boundary (after row 0 or a compressed row).
+ * Layout: int64 header {magic, Ly, next_row, layer, elem_bytes, bond[Ly+1],
+ * phys[Ly]}, double log_scale, then the tensors T_c in compute precision.
+ * With host_buf == NULL, *bytes receives the required size. */
+fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes);
+
+/* Load a boundary (same layout as fpeps_export_boundary, from any source with
+ * the right shapes) and make `next_row` the next row to absorb in `layer`.
+ * The tensors are copied host -> device on the env stream. */
+fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t bytes, int32_t next_row,
+                                   int32_t layer);
+
+/* Last error message of the env (never NULL; "" when none). */
+const char* fpeps_last_error(const fpeps_env* env);
+
+/* Release every resource of the env (safe on NULL). */
+void fpeps_env_destroy(fpeps_env* env);
+
+/* ---- diagnostics used by the tests (same arithmetic as the path) ---------- */
+
+/* Number of elements of the boundary tensor of site c (after the last step). */
+fpeps_status fpeps_boundary_shape(const fpeps_env* env, int32_t c, int32_t* t_left, int32_t* phys,
+                                  int32_t* t_right);
+
+/* Singular values kept at bond c by the last compress call (zip-up pass when
+ * which = 0, fit pass when which = 1); n_inout in: capacity, out: count. */
+fpeps_status fpeps_bond_spectrum(const fpeps_env* env, int32_t which, int32_t c, double* sv_host,
+                                 int32_t* n_inout);
+
+/* Apply one site's matrix Theta_c of the staged row to k host vectors:
+ * op 0: Y = Theta_c X, X [k][t_c * |R_c|] (column index t_c * |R_c| + R flat,
+ *       C order), Y [k][a * |Dn_c|] using the left environment `el_host`
+ *       [a][t_{c-1}][|L_c|] given by the caller.
+ * Element type = compute precision. Synchronises the stream. */
+fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void* el_host, int32_t k,
+                               const void* x_host, void* y_host);
+
+/* Library version string. */
+const char* fpeps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPEPS_H */

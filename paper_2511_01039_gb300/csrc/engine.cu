@@ -1,0 +1,854 @@
+// Row engine: boundary initialisation, zip-up rSVD compression, CBE fit and
+// the exact closing of the last row (paper Sec. II and Sec. IV).
+//
+// Layouts (device, compute precision T):
+//   boundary  T_c   [t][U][t']            (plus per-site copies [t'][t][U],
+//                                          [t][t'][U], [t'][U][t] for the GEMMs)
+//   left env  EL_c  [a][t][L]   and [t][L][a]
+//   right env ER_c  [a][t'][R]  and [t'][R][a]
+//   blocks of k vectors: [k][bundle][bond]  (bond fastest), e.g. X [k][R][t'],
+//   Y [k][Dn][a]; in C order of the (bond, bundle) legs the flat index of such
+//   a vector element is bond * |bundle| + bundle (this is the sketch counter).
+// Every contraction is a "TN" GEMM C(m,n) = sum_k A[m][k] B[n][k] with both
+// operands k-contiguous (Fig. 2(a) pattern: boundary x vectors, sandwich,
+// environment x vectors), sliced over the k vectors so that the O(chi^2 (DwD)^2)
+// intermediates of Sec. III never exist in full.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "env.cuh"
+
+namespace fpeps {
+
+template <class T>
+void col_signs(cudaStream_t s, const T* X, int64_t m, int n, int64_t ld, double* sgn);
+template <class T>
+void scale_cols(cudaStream_t s, T* X, int64_t m, int n, int64_t ld, const double* colscale);
+void svqb_factors(cudaStream_t s, const double* G, int k, double* work, double* Bt, double* Rq, int* info);
+void mul_vec(cudaStream_t s, const double* a, const double* b, double* out, int n);
+void gather_cols_f64(cudaStream_t s, const double* V, const int* order, int k, double* out);
+template <class T>
+void set_identity(cudaStream_t s, T* X, int64_t m, int n);
+template <class T>
+void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst);
+
+namespace {
+
+enum Orient { FWD = 0, BWD = 1, RF = 2, RB = 3 };
+const int kRoles[4][4] = {{1, 2, 0, 3}, {0, 3, 1, 2}, {2, 3, 0, 1}, {0, 1, 2, 3}};
+
+inline int bund(const SiteHost& h, int leg) { return h.dA[leg] * h.dW[leg] * h.dA[leg]; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ sandwich data
+void ensure_sandwich(fpeps_env* env, int layer, int row) {
+  const int Ly = env->cfg.Ly;
+  auto& sv = env->sand[layer];
+  if (sv.empty()) sv.resize((size_t)env->cfg.Lx * Ly);
+  for (int c = 0; c < Ly; ++c) {
+    const int idx = row * Ly + c;
+    SiteSand& sd = sv[idx];
+    if (!sd.bufs.empty()) continue;
+    const SiteHost& h = env->sites[layer][idx];
+    const int nch = (int)h.ch.size() / 4;
+    const int p = h.dA[4];
+    for (int o = 0; o < 4; ++o) {
+      const int* ro = kRoles[o];
+      // channels in role order, sorted by (v_w, z_w)
+      std::vector<std::array<int, 4>> rc;
+      for (int i = 0; i < nch; ++i) {
+        const int* v = &h.ch[4 * i];
+        rc.push_back({v[ro[0]], v[ro[1]], v[ro[2]], v[ro[3]]});
+      }
+      std::stable_sort(rc.begin(), rc.end(), [](const std::array<int, 4>& a, const std::array<int, 4>& b) {
+        return a[2] != b[2] ? a[2] < b[2] : a[3] < b[3];
+      });
+      SandOrient so{};
+      so.nx = h.dA[ro[0]]; so.nxw = h.dW[ro[0]];
+      so.ny = h.dA[ro[1]]; so.nyw = h.dW[ro[1]];
+      so.nv = h.dA[ro[2]]; so.nvw = h.dW[ro[2]];
+      so.nz = h.dA[ro[3]]; so.nzw = h.dW[ro[3]];
+      so.p = p;
+      so.nch = nch;
+      std::vector<int> flat, off((size_t)so.nvw * so.nzw + 1, 0);
+      for (auto& a : rc) {
+        flat.insert(flat.end(), a.begin(), a.end());
+        off[(size_t)a[2] * so.nzw + a[3] + 1]++;
+      }
+      int npair = 0;
+      for (size_t i = 1; i < off.size(); ++i) { npair += off[i] > 0; off[i] += off[i - 1]; }
+      if (o == FWD) sd.n_ld = npair;
+      int* d_ch = (int*)env->al.get(std::max<size_t>(flat.size(), 4) * sizeof(int));
+      int* d_off = (int*)env->al.get(off.size() * sizeof(int));
+      sd.bufs.push_back(d_ch);
+      sd.bufs.push_back(d_off);
+      if (!flat.empty()) FP_CUDA(cudaMemcpyAsync(d_ch, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, env->stream));
+      FP_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, env->stream));
+      size_t per = (size_t)so.nx * so.ny * so.nv * so.nz * p;
+      void* d_ar = env->al.get(per * env->elem);
+      void* d_aw = env->al.get(std::max<size_t>(per * nch, 1) * env->elem);
+      sd.bufs.push_back(d_ar);
+      sd.bufs.push_back(d_aw);
+      const char* A = (const char*)env->peps + h.offA * env->elem;
+      const char* W = (const char*)env->pepo[layer] + h.offW * env->elem;
+      if (env->elem == 8)
+        sandwich_prepare<double>(env->stream, (const double*)A, h.dA, (const double*)W, h.dW, ro, d_ch, nch,
+                                 (double*)d_aw, (double*)d_ar);
+      else
+        sandwich_prepare<float>(env->stream, (const float*)A, h.dA, (const float*)W, h.dW, ro, d_ch, nch,
+                                (float*)d_aw, (float*)d_ar);
+      so.d_ch = d_ch;
+      so.d_pair_off = d_off;
+      so.d_aw = d_aw;
+      so.d_ar = d_ar;
+      sd.o[o] = so;
+      // keep the host copy alive until the copies above have executed
+      FP_CUDA(cudaStreamSynchronize(env->stream));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ engine
+template <class T>
+struct Engine : EngineBase {
+  fpeps_env* env;
+  cudaStream_t s;
+  int mode;   // fpeps_precision
+  double flops = 0.0;
+  double trunc_num = 0.0, trunc_den = 0.0;
+  size_t budget_elems = (size_t)1 << 30;   // per-chunk intermediate size (elements)
+  void* scr[2] = {nullptr, nullptr};
+  size_t scr_n[2] = {0, 0};
+  void* tc_scr = nullptr;
+  size_t tc_n = 0;
+
+  explicit Engine(fpeps_env* e) : env(e), s(e->stream), mode(e->cfg.prec) {
+    if (const char* b = getenv("FPEPS_CHUNK_ELEMS")) budget_elems = (size_t)atoll(b);
+  }
+  ~Engine() override {
+    for (int i = 0; i < 2; ++i)
+      if (scr[i]) env->al.put(scr[i]);
+    if (tc_scr) env->al.put(tc_scr);
+  }
+
+  T* scratch(int i, size_t n) {
+    if (scr_n[i] < n) {
+      if (scr[i]) env->al.put(scr[i]);
+      scr[i] = env->al.get(n * sizeof(T));
+      scr_n[i] = n;
+    }
+    return (T*)scr[i];
+  }
+
+  // ---------------------------------------------------------------- GEMMs
+  // C = A B^T, A [M][lda], B [N][ldb], both k-contiguous
+  void big_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C, OutMap om) {
+    flops += 2.0 * (double)M * (double)N * (double)K;
+    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3)) {
+      FP_CHECK(gemm_tc_supported(M, N, K, lda, ldb), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: unsupported shape");
+      size_t need = gemm_tc_scratch_bytes(mode, M, N, K);
+      if (tc_n < need) {
+        if (tc_scr) env->al.put(tc_scr);
+        tc_scr = env->al.get(need);
+        tc_n = need;
+      }
+      gemm_tc(s, mode, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, om, tc_scr, tc_n);
+      return;
+    }
+    gemm_simt<T>(s, M, N, K, T(1), A, lda, 1, B, ldb, 1, T(0), C, om);
+  }
+
+  // column-major C (m x n, ldc) = op(A) op(B), alpha/beta (small products, CUDA cores)
+  void mm(int64_t m, int64_t n, int64_t k, T alpha, const T* A, bool ta, int64_t lda, const T* B, bool tb,
+          int64_t ldb, T beta, T* C, int64_t ldc) {
+    int64_t am = ta ? lda : 1, ak = ta ? 1 : lda;
+    int64_t bn = tb ? 1 : ldb, bk = tb ? ldb : 1;
+    gemm_simt<T>(s, m, n, k, alpha, A, am, ak, B, bn, bk, beta, C, out_colmajor(m, n, ldc));
+  }
+  void mm64(int64_t m, int64_t n, int64_t k, const double* A, bool ta, int64_t lda, const double* B, bool tb,
+            int64_t ldb, double* C, int64_t ldc) {
+    int64_t am = ta ? lda : 1, ak = ta ? 1 : lda;
+    int64_t bn = tb ? 1 : ldb, bk = tb ? ldb : 1;
+    gemm_simt<double>(s, m, n, k, 1.0, A, am, ak, B, bn, bk, 0.0, C, out_colmajor(m, n, ldc));
+  }
+
+  // ---------------------------------------------------------------- site operators
+  struct Site {
+    int c = 0, t = 1, tp = 1;
+    int bL = 1, bU = 1, bR = 1, bD = 1;
+    const T *Tm = nullptr, *Tt = nullptr, *Tp = nullptr, *Tq = nullptr;
+    const SiteSand* sd = nullptr;
+  };
+  struct Env3 {   // environment: [a][bond][bundle] and [bond][bundle][a]
+    int a = 1;
+    const T* E = nullptr;
+    const T* Et = nullptr;
+  };
+
+  double sand_flops(const SandOrient& o, int64_t blocks, int n_ld) const {
+    double ket = 2.0 * o.nch * (double)o.nx * o.nx * o.ny * o.ny * o.nv * o.nz * o.p;
+    double bra = 2.0 * n_ld * (double)o.nv * o.nv * o.nz * o.nz * o.nx * o.ny * o.p;
+    return (ket + bra) * (double)blocks;
+  }
+  int n_pairs(const SandOrient& o) {
+    std::vector<int> off((size_t)o.nvw * o.nzw + 1);
+    FP_CUDA(cudaMemcpy(off.data(), o.d_pair_off, off.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    int n = 0;
+    for (size_t i = 1; i < off.size(); ++i) n += off[i] > off[i - 1];
+    return n;
+  }
+
+  int64_t chunk_k(int64_t k, int64_t per_k) const {
+    int64_t kc = (int64_t)(budget_elems / (size_t)std::max<int64_t>(per_k, 1));
+    return std::max<int64_t>(1, std::min<int64_t>(k, kc));
+  }
+
+  // Y[k][Dn][a] = Theta_c X,  X[k][R][t']
+  void theta(const Site& st, const Env3& el, const T* X, T* Y, int64_t k) {
+    const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = el.a;
+    const SandOrient& o = st.sd->o[FWD];
+    const int64_t kc = chunk_k(k, t * std::max(U * R, L * Dn));
+    T* G1 = scratch(0, (size_t)(t * kc * U * R));
+    T* G2 = scratch(1, (size_t)(t * kc * L * Dn));
+    for (int64_t k0 = 0; k0 < k; k0 += kc) {
+      const int64_t kk = std::min(kc, k - k0);
+      big_gemm(t * U, kk * R, tp, st.Tm, tp, X + k0 * R * tp, tp, G1, OutMap{U, kk * U * R, R, R, U * R, 1});
+      sandwich_apply<T>(s, o, t, kk, G1, kk * U * R, U * R, R, 1, G2, L, Dn * t * L, 1, t * L);
+      flops += sand_flops(o, t * kk, st.sd->n_ld);
+      big_gemm(a, kk * Dn, t * L, el.E, t * L, G2, t * L, Y + k0 * Dn * a, OutMap{a, 0, 1, Dn, Dn * a, a});
+    }
+  }
+  // Z[k][R][t'] = Theta_c^T Y,  Y[k][Dn][a]
+  void theta_t(const Site& st, const Env3& el, const T* Y, T* Z, int64_t k) {
+    const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = el.a;
+    const SandOrient& o = st.sd->o[BWD];
+    const int64_t kc = chunk_k(k, t * std::max(U * R, L * Dn));
+    T* H1 = scratch(0, (size_t)(t * kc * L * Dn));
+    T* H2 = scratch(1, (size_t)(t * kc * U * R));
+    for (int64_t k0 = 0; k0 < k; k0 += kc) {
+      const int64_t kk = std::min(kc, k - k0);
+      big_gemm(t * L, kk * Dn, a, el.Et, a, Y + k0 * Dn * a, a, H1, OutMap{L, kk * L * Dn, Dn, Dn, L * Dn, 1});
+      sandwich_apply<T>(s, o, t, kk, H1, kk * L * Dn, L * Dn, Dn, 1, H2, U, R * t * U, 1, t * U);
+      flops += sand_flops(o, t * kk, st.sd->n_ld);
+      big_gemm(tp, kk * R, t * U, st.Tt, t * U, H2, t * U, Z + k0 * R * tp, OutMap{tp, 0, 1, R, R * tp, tp});
+    }
+  }
+  // Z[k][L][t] = ThetaR_c X,  X[k][Dn][a_c]; er = environment to the right of site c
+  void theta_r(const Site& st, const Env3& er, const T* X, T* Z, int64_t k) {
+    const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = er.a;
+    const SandOrient& o = st.sd->o[RF];
+    const int64_t kc = chunk_k(k, tp * std::max(R * Dn, L * U));
+    T* W1 = scratch(0, (size_t)(tp * kc * R * Dn));
+    T* W2 = scratch(1, (size_t)(tp * kc * L * U));
+    for (int64_t k0 = 0; k0 < k; k0 += kc) {
+      const int64_t kk = std::min(kc, k - k0);
+      big_gemm(tp * R, kk * Dn, a, er.Et, a, X + k0 * Dn * a, a, W1, OutMap{R, kk * R * Dn, Dn, Dn, R * Dn, 1});
+      sandwich_apply<T>(s, o, tp, kk, W1, kk * R * Dn, R * Dn, Dn, 1, W2, U, L * tp * U, tp * U, 1);
+      flops += sand_flops(o, tp * kk, st.sd->n_ld);
+      big_gemm(t, kk * L, tp * U, st.Tp, tp * U, W2, tp * U, Z + k0 * L * t, OutMap{t, 0, 1, L, L * t, t});
+    }
+  }
+  // X[k][Dn][a_c] = ThetaR_c^T Z,  Z[k][L][t]
+  void theta_r_t(const Site& st, const Env3& er, const T* Z, T* X, int64_t k) {
+    const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = er.a;
+    const SandOrient& o = st.sd->o[RB];
+    const int64_t kc = chunk_k(k, tp * std::max(R * Dn, L * U));
+    T* W1 = scratch(0, (size_t)(tp * kc * L * U));
+    T* W2 = scratch(1, (size_t)(tp * kc * R * Dn));
+    for (int64_t k0 = 0; k0 < k; k0 += kc) {
+      const int64_t kk = std::min(kc, k - k0);
+      big_gemm(tp * U, kk * L, t, st.Tq, t, Z + k0 * L * t, t, W1, OutMap{U, kk * L * U, 1, L, L * U, U});
+      sandwich_apply<T>(s, o, tp, kk, W1, kk * L * U, L * U, U, 1, W2, R, Dn * tp * R, 1, tp * R);
+      flops += sand_flops(o, tp * kk, st.sd->n_ld);
+      big_gemm(a, kk * Dn, tp * R, er.E, tp * R, W2, tp * R, X + k0 * Dn * a, OutMap{a, 0, 1, Dn, Dn * a, a});
+    }
+  }
+
+  // ---------------------------------------------------------------- helpers
+  Arena arena() { Arena ar; ar.al = &env->al; return ar; }
+
+  double host_norm(const T* x, int64_t n) {
+    frob_norm_f64<T>(s, x, n, env->d_scal);
+    FP_CUDA(cudaMemcpyAsync(env->h_scal, env->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+    double v = env->h_scal[0];
+    FP_CHECK(std::isfinite(v), FPEPS_ERR_NUMERIC, "non-finite norm");
+    return v;
+  }
+  int read_info() {
+    FP_CUDA(cudaMemcpyAsync(env->h_info, env->d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+    return env->h_info[0];
+  }
+
+  Site make_site(Arena& ar, int row, int c, bool need_fwd, bool need_r) {
+    Site st;
+    st.c = c;
+    const SiteHost& h = env->sites[env->layer][row * env->cfg.Ly + c];
+    st.bL = bund(h, 0); st.bU = bund(h, 1); st.bR = bund(h, 2); st.bD = bund(h, 3);
+    st.t = env->tb[c];
+    st.tp = env->tb[c + 1];
+    FP_CHECK(env->tphys[c] == st.bU, FPEPS_ERR_ARG, "boundary bundle does not match the row's up legs");
+    st.sd = &env->sand[env->layer][row * env->cfg.Ly + c];
+    const T* Tm = (const T*)env->T[c];
+    st.Tm = Tm;
+    const int64_t t = st.t, U = st.bU, tp = st.tp;
+    if (need_fwd) {
+      T* Tt = ar.get_n<T>(t * U * tp);
+      permute3<T>(s, Tm, Tt, t, U, tp, 2, 0, 1);
+      st.Tt = Tt;
+    }
+    if (need_r) {
+      T* Tp = ar.get_n<T>(t * U * tp);
+      T* Tq = ar.get_n<T>(t * U * tp);
+      permute3<T>(s, Tm, Tp, t, U, tp, 0, 2, 1);
+      permute3<T>(s, Tm, Tq, t, U, tp, 2, 1, 0);
+      st.Tp = Tp;
+      st.Tq = Tq;
+    }
+    return st;
+  }
+
+  // env tensors from a vector block V[a][bundle][bond] (a vectors): E [a][bond][bundle], Et [bond][bundle][a]
+  Env3 env_from_vectors(Arena& ar, const T* Vb, int a, int64_t bundle, int64_t bond) {
+    Env3 e;
+    e.a = a;
+    T* E = ar.get_n<T>((int64_t)a * bundle * bond);
+    T* Et = ar.get_n<T>((int64_t)a * bundle * bond);
+    permute3<T>(s, Vb, E, a, bundle, bond, 0, 2, 1);
+    permute3<T>(s, Vb, Et, a, bundle, bond, 2, 1, 0);
+    e.E = E;
+    e.Et = Et;
+    return e;
+  }
+  Env3 unit_env(Arena& ar) {
+    T* one = ar.get_n<T>(1);
+    fill<T>(s, one, 1, T(1));
+    Env3 e;
+    e.a = 1;
+    e.E = one;
+    e.Et = one;
+    return e;
+  }
+
+  // ---------------------------------------------------------------- QR (Sec. IV)
+  // Y (m x k, col-major, ld = m) = Q R. CholeskyQR2 in FP64 (Gram, Cholesky,
+  // Q = Y R^-1, twice); a pass whose Cholesky breaks down uses SVQB instead
+  // (eigenvectors of the scaled Gram, directions with eigenvalue below
+  // 1e-15 of the largest become zero columns). R: k x k row-major FP64, or null.
+  void one_pass(Arena& ar, const T* Y, int64_t m, int k, T* Q, double* R) {
+    double* G = ar.get_n<double>((int64_t)k * k);
+    gram_f64<T>(s, Y, m, k, m, G);
+    cholesky_upper_f64(s, G, k, env->d_info);
+    T* Bt = ar.get_n<T>((int64_t)k * k);
+    if (read_info() == 0) {
+      double* Rinv = ar.get_n<double>((int64_t)k * k);
+      tri_inverse_upper_f64(s, G, k, Rinv);
+      convert_f64<T>(s, Rinv, Bt, (int64_t)k * k);
+      // Q(m, j) = sum_i Y(m, i) Rinv(i, j);  Rinv row-major
+      gemm_simt<T>(s, m, k, k, T(1), Y, 1, m, Bt, 1, k, T(0), Q, out_colmajor(m, k, m));
+      if (R) FP_CUDA(cudaMemcpyAsync(R, G, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
+      return;
+    }
+    // SVQB
+    gram_f64<T>(s, Y, m, k, m, G);
+    double* work = ar.get_n<double>((int64_t)6 * k * k + 4 * k);
+    double* Bt64 = ar.get_n<double>((int64_t)k * k);
+    double* Rq = ar.get_n<double>((int64_t)k * k);
+    svqb_factors(s, G, k, work, Bt64, Rq, env->d_info);
+    FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "QR: eigen-decomposition did not converge");
+    convert_f64<T>(s, Bt64, Bt, (int64_t)k * k);
+    // Q(m, j) = sum_i Y(m, i) Bt(i, j), Bt col-major
+    gemm_simt<T>(s, m, k, k, T(1), Y, 1, m, Bt, k, 1, T(0), Q, out_colmajor(m, k, m));
+    if (R) FP_CUDA(cudaMemcpyAsync(R, Rq, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
+  }
+
+  void qr(const T* Y, int64_t m, int k, T* Q, double* R) {
+    Arena ar = arena();
+    T* Q1 = ar.get_n<T>(m * k);
+    double* R1 = R ? ar.get_n<double>((int64_t)k * k) : nullptr;
+    double* R2 = R ? ar.get_n<double>((int64_t)k * k) : nullptr;
+    one_pass(ar, Y, m, k, Q1, R1);
+    one_pass(ar, Q1, m, k, Q, R2);
+    if (R) {   // R = R2 R1 (row-major)
+      gemm_simt<double>(s, k, k, k, 1.0, R2, k, 1, R1, 1, k, 0.0, R, out_rowmajor(k, k, k));
+    }
+  }
+
+  // ---------------------------------------------------------------- rSVD (Sec. IV)
+  struct Lin {
+    int64_t m, n;
+    std::function<void(const T*, T*, int64_t)> fwd, bwd;
+  };
+  struct RsvdOut {
+    T* Q;        // m x k
+    T* QbW;      // n x k  right singular vectors (sorted)
+    double* U;   // k x k  left singular vectors in the Q basis, col-major (sorted)
+    std::vector<double> sigma;
+  };
+  // Randomized subspace iteration with re-orthonormalisation after every
+  // application, then B = Q^T A = R_b^T Q_b^T and the Jacobi SVD of R_b^T.
+  RsvdOut rsvd(Arena& ar, Lin& A, const T* omega, int k, int q) {
+    RsvdOut r;
+    const int64_t m = A.m, n = A.n;
+    T* Y = ar.get_n<T>(m * k);
+    T* Z = ar.get_n<T>(n * k);
+    r.Q = ar.get_n<T>(m * k);
+    T* Qz = ar.get_n<T>(n * k);
+    A.fwd(omega, Y, k);
+    qr(Y, m, k, r.Q, nullptr);
+    for (int it = 0; it < q; ++it) {
+      A.bwd(r.Q, Z, k);
+      qr(Z, n, k, Qz, nullptr);
+      A.fwd(Qz, Y, k);
+      qr(Y, m, k, r.Q, nullptr);
+    }
+    A.bwd(r.Q, Z, k);                       // B^T = A^T Q  (n x k)
+    double* Rb = ar.get_n<double>((int64_t)k * k);
+    qr(Z, n, k, Qz, Rb);                    // B^T = Q_b R_b
+    // SVD of R_b^T: the row-major R_b array read as col-major is R_b^T
+    double* Ms = ar.get_n<double>((int64_t)k * k);
+    FP_CUDA(cudaMemcpyAsync(Ms, Rb, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
+    double* Uj = ar.get_n<double>((int64_t)k * k);
+    double* Vj = ar.get_n<double>((int64_t)k * k);
+    double* sg = ar.get_n<double>(k);
+    int* order = ar.get_n<int>(k);
+    svd_jacobi_f64(s, Ms, k, Uj, sg, Vj, order, env->d_info);
+    FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "Jacobi SVD did not converge");
+    r.U = Uj;
+    double* Vs = ar.get_n<double>((int64_t)k * k);
+    gather_cols_f64(s, Vj, order, k, Vs);
+    T* Vt = ar.get_n<T>((int64_t)k * k);
+    convert_f64<T>(s, Vs, Vt, (int64_t)k * k);
+    r.QbW = ar.get_n<T>(n * k);
+    mm(n, k, k, T(1), Qz, false, n, Vt, false, k, T(0), r.QbW, n);
+    r.sigma.resize(k);
+    FP_CUDA(cudaMemcpyAsync(r.sigma.data(), sg, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+    return r;
+  }
+
+  // ---------------------------------------------------------------- row 0 / last row
+  void first_row(fpeps_env* e, int row) override {
+    const int Ly = e->cfg.Ly;
+    std::vector<int> tb(Ly + 1, 1), ph(Ly, 1);
+    std::vector<void*> T_new(Ly, nullptr);
+    double log_s = 0.0;
+    for (int c = 0; c < Ly; ++c) {
+      const SiteHost& h = e->sites[e->layer][row * Ly + c];
+      const int64_t nL = bund(h, 0), nD = bund(h, 3), nR = bund(h, 2);
+      T* out = (T*)e->al.get(sizeof(T) * nL * nD * nR);
+      const T* A = (const T*)((const char*)e->peps + h.offA * e->elem);
+      const T* W = (const T*)((const char*)e->pepo[e->layer] + h.offW * e->elem);
+      first_row_tensor<T>(s, A, h.dA, W, h.dW, out);
+      double nrm = host_norm(out, nL * nD * nR);
+      FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "row-0 site tensor is zero");
+      scale_by_inv<T>(s, out, nL * nD * nR, e->d_scal);
+      log_s += std::log(nrm);
+      T_new[c] = out;
+      tb[c] = (int)nL;
+      tb[c + 1] = (int)nR;
+      ph[c] = (int)nD;
+    }
+    for (void* p : e->T) e->al.put(p);
+    e->T = T_new;
+    e->tb = tb;
+    e->tphys = ph;
+    e->log_scale += log_s;
+  }
+
+  void close_row(fpeps_env* e, int row) override {
+    const int Ly = e->cfg.Ly;
+    ensure_sandwich(e, e->layer, row);
+    Arena keep = arena();
+    Env3 v = unit_env(keep);
+    T* ones = keep.get_n<T>(1);
+    fill<T>(s, ones, 1, T(1));
+    double log_s = 0.0, val = 0.0;
+    for (int c = 0; c < Ly; ++c) {
+      Arena ar = arena();
+      Site st = make_site(ar, row, c, true, false);
+      FP_CHECK(st.bD == 1, FPEPS_ERR_ARG, "last row must have dimension-1 down legs");
+      T* Z = ar.get_n<T>((int64_t)st.bR * st.tp);
+      theta_t(st, v, ones, Z, 1);
+      const int64_t n = (int64_t)st.bR * st.tp;
+      if (c < Ly - 1) {
+        double nrm = host_norm(Z, n);
+        FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "closing vector vanished");
+        scale_by_inv<T>(s, Z, n, e->d_scal);
+        log_s += std::log(nrm);
+        Arena nk = arena();
+        Env3 nv = env_from_vectors(nk, Z, 1, st.bR, st.tp);
+        FP_CUDA(cudaStreamSynchronize(s));
+        keep.reset();
+        keep.live = nk.live;   // transfer ownership
+        nk.live.clear();
+        v = nv;
+        T* o2 = keep.get_n<T>(1);
+        fill<T>(s, o2, 1, T(1));
+        ones = o2;
+      } else {
+        T hv;
+        FP_CUDA(cudaMemcpyAsync(&hv, Z, sizeof(T), cudaMemcpyDeviceToHost, s));
+        FP_CUDA(cudaStreamSynchronize(s));
+        val = (double)hv;
+      }
+      FP_CUDA(cudaStreamSynchronize(s));
+    }
+    FP_CHECK(std::isfinite(val), FPEPS_ERR_NUMERIC, "non-finite closing value");
+    e->value_sign = val >= 0 ? 1 : -1;
+    e->value_log = e->log_scale + log_s + (val != 0 ? std::log(std::fabs(val)) : -INFINITY);
+    e->have_value = true;
+  }
+
+  // ---------------------------------------------------------------- compression
+  void compress(fpeps_env* e, int row, const fpeps_rsvd_params& prm, fpeps_stats* out) override {
+    const int Ly = e->cfg.Ly;
+    const int chi = e->cfg.chi;
+    ensure_sandwich(e, e->layer, row);
+    flops = 0.0;
+    trunc_num = trunc_den = 0.0;
+    cudaEvent_t ev0, ev1;
+    FP_CUDA(cudaEventCreate(&ev0));
+    FP_CUDA(cudaEventCreate(&ev1));
+    FP_CUDA(cudaEventRecord(ev0, s));
+    e->spectra.zip.assign(Ly, {});
+    e->spectra.fit.assign(Ly, {});
+
+    Arena rowmem = arena();                      // lives for the whole row
+    std::vector<T*> Nvec(Ly, nullptr);           // zip-up isometries as vectors [chi][Dn][a]
+    std::vector<int> abond(Ly + 1, 1);           // new bonds
+    std::vector<Env3> EL(Ly);
+    std::vector<T*> ELvec(Ly, nullptr);
+    EL[0] = unit_env(rowmem);
+    double log_s = 0.0;
+    const uint64_t w3 = (uint64_t)row;
+
+    // ---------------- zip-up, left to right
+    for (int c = 0; c < Ly - 1; ++c) {
+      Arena ar = arena();
+      Site st = make_site(ar, row, c, true, false);
+      const int a = EL[c].a;
+      const int64_t rows = (int64_t)a * st.bD, cols = (int64_t)st.tp * st.bR;
+      const int chi_c = (int)std::min<int64_t>({(int64_t)chi, rows, cols});
+      const int k = prm.exact_svd ? (int)std::min(rows, cols)
+                                  : (int)std::min<int64_t>({(int64_t)chi_c + prm.oversample, rows, cols});
+      T* omega = ar.get_n<T>(cols * k);
+      int64_t perm[2] = {st.bR, st.tp};
+      gaussian_sketch<T>(s, omega, cols, k, cols, perm, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c, w3);
+      Env3 elc = EL[c];
+      Lin A{rows, cols,
+            [&](const T* X, T* Y, int64_t kk) { theta(st, elc, X, Y, kk); },
+            [&](const T* Y, T* Z, int64_t kk) { theta_t(st, elc, Y, Z, kk); }};
+      RsvdOut r = rsvd(ar, A, omega, k, prm.power_iters);
+      // N = Q U[:, :chi_c]
+      T* Ut = ar.get_n<T>((int64_t)k * k);
+      convert_f64<T>(s, r.U, Ut, (int64_t)k * k);
+      T* N = rowmem.get_n<T>(rows * chi_c);
+      mm(rows, chi_c, k, T(1), r.Q, false, rows, Ut, false, k, T(0), N, rows);
+      double* sgn = ar.get_n<double>(chi_c);
+      col_signs<T>(s, N, rows, chi_c, rows, sgn);
+      scale_cols<T>(s, N, rows, chi_c, rows, sgn);
+      // EL_{c+1} vectors = Q_b W[:, :chi] diag(sigma * sign)
+      double* sc = ar.get_n<double>(chi_c);
+      double* sgd = ar.get_n<double>(chi_c);
+      FP_CUDA(cudaMemcpyAsync(sgd, r.sigma.data(), sizeof(double) * chi_c, cudaMemcpyHostToDevice, s));
+      mul_vec(s, sgd, sgn, sc, chi_c);
+      T* elv = rowmem.get_n<T>(cols * chi_c);
+      FP_CUDA(cudaMemcpyAsync(elv, r.QbW, sizeof(T) * cols * chi_c, cudaMemcpyDeviceToDevice, s));
+      scale_cols<T>(s, elv, cols, chi_c, cols, sc);
+      double nrm = host_norm(elv, cols * chi_c);
+      FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "zip-up remainder vanished");
+      scale_by_inv<T>(s, elv, cols * chi_c, e->d_scal);
+      log_s += std::log(nrm);
+      for (int j = 0; j < (int)r.sigma.size(); ++j) {
+        double v2 = r.sigma[j] * r.sigma[j];
+        trunc_den += v2;
+        if (j >= chi_c) trunc_num += v2;
+      }
+      e->spectra.zip[c].assign(r.sigma.begin(), r.sigma.begin() + chi_c);
+      Nvec[c] = N;
+      abond[c + 1] = chi_c;
+      ELvec[c + 1] = elv;
+      EL[c + 1] = env_from_vectors(rowmem, elv, chi_c, st.bR, st.tp);
+      FP_CUDA(cudaStreamSynchronize(s));
+    }
+    // last site: Theta has a single column
+    T* Nlast = nullptr;
+    {
+      Arena ar = arena();
+      const int c = Ly - 1;
+      Site st = make_site(ar, row, c, true, false);
+      T* one = ar.get_n<T>(1);
+      fill<T>(s, one, 1, T(1));
+      const int64_t rows = (int64_t)EL[c].a * st.bD;
+      Nlast = rowmem.get_n<T>(rows);
+      theta(st, EL[c], one, Nlast, 1);
+      double nrm = host_norm(Nlast, rows);
+      FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "zip-up last tensor vanished");
+      scale_by_inv<T>(s, Nlast, rows, e->d_scal);
+      log_s += std::log(nrm);
+      FP_CUDA(cudaStreamSynchronize(s));
+    }
+
+    std::vector<void*> T_new(Ly, nullptr);
+    std::vector<int> tb_new(Ly + 1, 1), ph_new(Ly, 1);
+    for (int c = 0; c < Ly; ++c) ph_new[c] = bund(e->sites[e->layer][row * Ly + c], 3);
+    double log_row = log_s;
+
+    if (prm.n_fit == 0 || Ly == 1) {
+      // boundary = zip-up isometries [a][Dn][chi] and the last tensor [a][Dn][1]
+      for (int c = 0; c < Ly; ++c) {
+        const int a = abond[c], b = (c < Ly - 1) ? abond[c + 1] : 1, Dn = ph_new[c];
+        T* out = (T*)e->al.get(sizeof(T) * (int64_t)a * Dn * b);
+        if (c < Ly - 1)
+          permute3<T>(s, Nvec[c], out, b, Dn, a, 2, 1, 0);
+        else
+          FP_CUDA(cudaMemcpyAsync(out, Nlast, sizeof(T) * (int64_t)a * Dn, cudaMemcpyDeviceToDevice, s));
+        T_new[c] = out;
+        tb_new[c] = a;
+        tb_new[c + 1] = b;
+      }
+    } else {
+      if (prm.n_fit != 1) throw Error{FPEPS_ERR_UNSUPPORTED, "n_fit must be 0 or 1"};
+      log_row = fit(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem);
+    }
+    FP_CUDA(cudaStreamSynchronize(s));
+    for (void* p : e->T) e->al.put(p);
+    e->T = T_new;
+    e->tb = tb_new;
+    e->tphys = ph_new;
+    e->log_scale += log_row;
+    FP_CUDA(cudaEventRecord(ev1, s));
+    FP_CUDA(cudaEventSynchronize(ev1));
+    float ms = 0;
+    FP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (out) {
+      out->seconds = ms * 1e-3;
+      out->alg_flops = flops;
+      out->log_scale = log_row;
+      out->trunc_err_est = trunc_den > 0 ? trunc_num / trunc_den : 0.0;
+    }
+  }
+
+  // Right-to-left variational fit with controlled bond expansion (Fig. 3-5).
+  double fit(int row, const fpeps_rsvd_params& prm, std::vector<T*>& Nvec, std::vector<int>& abond,
+             std::vector<Env3>& EL, T* Nlast, std::vector<void*>& T_new, std::vector<int>& tb_new, Arena& rowmem) {
+    fpeps_env* e = env;
+    const int Ly = e->cfg.Ly;
+    const int chi = e->cfg.chi;
+    const int chi_t = prm.chi_tilde > 0 ? prm.chi_tilde : (chi + 9) / 10;
+    const uint64_t w3 = (uint64_t)row;
+    // centre M [a_prev][Dn][a_c] as vectors (a_prev of them)
+    Arena mmem = arena();
+    int a_prev = abond[Ly - 1];
+    int a_c = 1;
+    const int64_t nlast = (int64_t)a_prev * bund(e->sites[e->layer][row * Ly + Ly - 1], 3);
+    T* M = mmem.get_n<T>(nlast);
+    FP_CUDA(cudaMemcpyAsync(M, Nlast, sizeof(T) * nlast, cudaMemcpyDeviceToDevice, s));
+    // Nlast is [a][Dn][1] flat = vectors [a][Dn*1]: already "a_prev vectors of (Dn, a_c=1)"
+    Arena ermem = arena();
+    Env3 ER = unit_env(ermem);
+    double rs = 0.0, rs_M = 0.0;
+    for (int c = Ly - 1; c >= 1; --c) {
+      Arena ar = arena();
+      Site sc = make_site(ar, row, c, false, true);
+      Site sl = make_site(ar, row, c - 1, true, false);
+      const int Dn = sc.bD;
+      const int64_t cols_a = (int64_t)Dn * a_c;
+      // V^T = orth(M^T): (Dn a_c) x a_prev
+      int a_eff;
+      T* VT;
+      if (a_prev >= cols_a) {
+        a_eff = (int)cols_a;
+        VT = ar.get_n<T>(cols_a * a_eff);
+        set_identity<T>(s, VT, cols_a, a_eff);
+      } else {
+        a_eff = a_prev;
+        VT = ar.get_n<T>(cols_a * a_eff);
+        qr(M, cols_a, a_eff, VT, nullptr);
+      }
+      const int a2 = EL[c - 1].a;
+      const int Dnl = sl.bD;
+      const int64_t rows_a = (int64_t)a2 * Dnl;
+      const int na = abond[c];          // columns of the zip-up isometry at c-1
+      T* Nl = Nvec[c - 1];              // rows_a x na
+      const int ct = (int)std::min<int64_t>({(int64_t)chi_t, rows_a - na, cols_a - a_eff});
+      Env3 elc = EL[c - 1];
+      Env3 erc = ER;
+      T* Vp;
+      int j;
+      if (ct > 0) {
+        const int k = (int)std::min<int64_t>({(int64_t)ct + prm.oversample, rows_a, cols_a});
+        T* omega = ar.get_n<T>(cols_a * k);
+        gaussian_sketch<T>(s, omega, cols_a, k, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer,
+                           (uint64_t)c | (1ull << 16), w3);
+        const int kmax = k;
+        T* tmpA = ar.get_n<T>(std::max<int64_t>(a_eff, na) * kmax);
+        T* Xp = ar.get_n<T>(std::max(cols_a, rows_a) * kmax);
+        T* Zm = ar.get_n<T>(((int64_t)sl.tp * sl.bR) * kmax);
+        auto projR = [&](const T* X, T* out, int64_t kk) {   // out = X - V^T (V X)
+          mm(a_eff, kk, cols_a, T(1), VT, true, cols_a, X, false, cols_a, T(0), tmpA, a_eff);
+          FP_CUDA(cudaMemcpyAsync(out, X, sizeof(T) * cols_a * kk, cudaMemcpyDeviceToDevice, s));
+          mm(cols_a, kk, a_eff, T(-1), VT, false, cols_a, tmpA, false, a_eff, T(1), out, cols_a);
+        };
+        auto projL = [&](T* Y, int64_t kk) {   // Y -= Nl (Nl^T Y)
+          mm(na, kk, rows_a, T(1), Nl, true, rows_a, Y, false, rows_a, T(0), tmpA, na);
+          mm(rows_a, kk, na, T(-1), Nl, false, rows_a, tmpA, false, na, T(1), Y, rows_a);
+        };
+        Lin A{rows_a, cols_a,
+              [&](const T* X, T* Y, int64_t kk) {
+                projR(X, Xp, kk);
+                theta_r(sc, erc, Xp, Zm, kk);
+                theta(sl, elc, Zm, Y, kk);
+                projL(Y, kk);
+              },
+              [&](const T* Y, T* X, int64_t kk) {
+                FP_CUDA(cudaMemcpyAsync(Xp, Y, sizeof(T) * rows_a * kk, cudaMemcpyDeviceToDevice, s));
+                projL(Xp, kk);
+                theta_t(sl, elc, Xp, Zm, kk);
+                theta_r_t(sc, erc, Zm, X, kk);
+                // X -= V^T (V X)
+                mm(a_eff, kk, cols_a, T(1), VT, true, cols_a, X, false, cols_a, T(0), tmpA, a_eff);
+                mm(cols_a, kk, a_eff, T(-1), VT, false, cols_a, tmpA, false, a_eff, T(1), X, cols_a);
+              }};
+        RsvdOut r = rsvd(ar, A, omega, k, prm.power_iters);
+        // V' = orth([V^T | Vtil^T])
+        j = a_eff + ct;
+        T* cat = ar.get_n<T>(cols_a * j);
+        copy_cols<T>(s, VT, cols_a, a_eff, cat);
+        copy_cols<T>(s, r.QbW, cols_a, ct, cat + cols_a * a_eff);
+        Vp = ar.get_n<T>(cols_a * j);
+        qr(cat, cols_a, j, Vp, nullptr);
+      } else {
+        j = a_eff;
+        Vp = VT;
+      }
+      // expanded right environment and the fitted tensor at c-1 (pattern 2(a))
+      const int64_t nER = (int64_t)sl.tp * sl.bR;    // (t_{c-1}, L_c) space
+      T* ERp = ar.get_n<T>(nER * j);
+      theta_r(sc, erc, Vp, ERp, j);
+      T* Mp = ar.get_n<T>(rows_a * j);
+      theta(sl, elc, ERp, Mp, j);
+      const int keep = (int)std::min<int64_t>({(int64_t)chi, rows_a, (int64_t)j});
+      // SVD of M' = Q_m R_m,  R_m = U_r S W^T  (Jacobi on R_m^T: U_jac = W, V_jac = U_r)
+      T* Qm = ar.get_n<T>(rows_a * j);
+      double* Rm = ar.get_n<double>((int64_t)j * j);
+      qr(Mp, rows_a, j, Qm, Rm);
+      double* Uj = ar.get_n<double>((int64_t)j * j);
+      double* Vj = ar.get_n<double>((int64_t)j * j);
+      double* sg = ar.get_n<double>(j);
+      int* order = ar.get_n<int>(j);
+      svd_jacobi_f64(s, Rm, j, Uj, sg, Vj, order, e->d_info);
+      FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "Jacobi SVD did not converge (fit)");
+      double* Vs = ar.get_n<double>((int64_t)j * j);
+      gather_cols_f64(s, Vj, order, j, Vs);
+      T* Wt = ar.get_n<T>((int64_t)j * j);
+      T* Urt = ar.get_n<T>((int64_t)j * j);
+      convert_f64<T>(s, Uj, Wt, (int64_t)j * j);
+      convert_f64<T>(s, Vs, Urt, (int64_t)j * j);
+      // new right isometry N_c^T = V' W[:, :keep]  ->  [keep][Dn][a_c]
+      T* Nc = (T*)e->al.get(sizeof(T) * cols_a * keep);
+      mm(cols_a, keep, j, T(1), Vp, false, cols_a, Wt, false, j, T(0), Nc, cols_a);
+      double* sgn = ar.get_n<double>(keep);
+      col_signs<T>(s, Nc, cols_a, keep, cols_a, sgn);
+      scale_cols<T>(s, Nc, cols_a, keep, cols_a, sgn);
+      T_new[c] = Nc;
+      tb_new[c] = keep;
+      tb_new[c + 1] = a_c;
+      // M_{c-1} = Q_m U_r[:, :keep] diag(S sign)  (vectors [keep][Dnl][a2]) -> [a2][Dnl][keep]
+      double* scl = ar.get_n<double>(keep);
+      mul_vec(s, sg, sgn, scl, keep);
+      T* Mv = ar.get_n<T>(rows_a * keep);
+      mm(rows_a, keep, j, T(1), Qm, false, rows_a, Urt, false, j, T(0), Mv, rows_a);
+      scale_cols<T>(s, Mv, rows_a, keep, rows_a, scl);
+      Arena mnew = arena();
+      T* Mnext = mnew.get_n<T>(rows_a * keep);
+      permute3<T>(s, Mv, Mnext, keep, Dnl, a2, 2, 1, 0);
+      // ER_c vectors = ER' W[:, :keep] diag(sign)  -> [keep][L][t]
+      T* erv = ar.get_n<T>(nER * keep);
+      mm(nER, keep, j, T(1), ERp, false, nER, Wt, false, j, T(0), erv, nER);
+      scale_cols<T>(s, erv, nER, keep, nER, sgn);
+      double nrm = host_norm(erv, nER * keep);
+      FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "right environment vanished");
+      scale_by_inv<T>(s, erv, nER * keep, e->d_scal);
+      rs_M = rs;
+      rs += std::log(nrm);
+      Arena ernew = arena();
+      Env3 ERn = env_from_vectors(ernew, erv, keep, sl.bR, sl.tp);
+      {
+        std::vector<double> sv(j);
+        FP_CUDA(cudaMemcpyAsync(sv.data(), sg, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+        FP_CUDA(cudaStreamSynchronize(s));
+        e->spectra.fit[c - 1].assign(sv.begin(), sv.begin() + keep);
+      }
+      FP_CUDA(cudaStreamSynchronize(s));
+      // rotate ownership
+      ermem.reset();
+      ermem.live = ernew.live;
+      ernew.live.clear();
+      ER = ERn;
+      mmem.reset();
+      mmem.live = mnew.live;
+      mnew.live.clear();
+      M = Mnext;
+      a_c = keep;
+      a_prev = a2;
+    }
+    // site 0: M_0 [1][Dn_0][a_0]
+    const int Dn0 = bund(e->sites[e->layer][row * Ly], 3);
+    const int64_t n0 = (int64_t)Dn0 * a_c;
+    double nrm = host_norm(M, n0);
+    FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "fit centre vanished");
+    T* N0 = (T*)e->al.get(sizeof(T) * n0);
+    FP_CUDA(cudaMemcpyAsync(N0, M, sizeof(T) * n0, cudaMemcpyDeviceToDevice, s));
+    scale_by_inv<T>(s, N0, n0, e->d_scal);
+    T_new[0] = N0;
+    tb_new[0] = 1;
+    tb_new[1] = a_c;
+    FP_CUDA(cudaStreamSynchronize(s));
+    return rs_M + std::log(nrm);
+  }
+
+  // ---------------------------------------------------------------- diagnostics
+  void apply_theta_host(fpeps_env* e, int c, int a, const void* el, int k, const void* x, void* y) override {
+    const int row = e->staged_row;
+    FP_CHECK(row > 0, FPEPS_ERR_STATE, "no staged row");
+    ensure_sandwich(e, e->layer, row);
+    Arena ar = arena();
+    Site st = make_site(ar, row, c, true, false);
+    const int64_t t = st.t, L = st.bL, tp = st.tp, R = st.bR, Dn = st.bD;
+    // el [a][t][L]; x [k][t'][R]; y [k][a][Dn]  (host, C order)
+    T* elv = ar.get_n<T>((int64_t)a * t * L);
+    FP_CUDA(cudaMemcpyAsync(elv, el, sizeof(T) * a * t * L, cudaMemcpyHostToDevice, s));
+    Env3 E;
+    E.a = a;
+    E.E = elv;
+    T* Et = ar.get_n<T>((int64_t)a * t * L);
+    permute3<T>(s, elv, Et, a, t, L, 1, 2, 0);
+    E.Et = Et;
+    T* xh = ar.get_n<T>((int64_t)k * tp * R);
+    FP_CUDA(cudaMemcpyAsync(xh, x, sizeof(T) * k * tp * R, cudaMemcpyHostToDevice, s));
+    T* X = ar.get_n<T>((int64_t)k * tp * R);
+    permute3<T>(s, xh, X, k, tp, R, 0, 2, 1);
+    T* Y = ar.get_n<T>((int64_t)k * Dn * a);
+    theta(st, E, X, Y, k);
+    T* yh = ar.get_n<T>((int64_t)k * Dn * a);
+    permute3<T>(s, Y, yh, k, Dn, a, 0, 2, 1);
+    FP_CUDA(cudaMemcpyAsync(y, yh, sizeof(T) * k * Dn * a, cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+  }
+};
+
+EngineBase* make_engine(fpeps_env* env) {
+  if (env->elem == 8) return new Engine<double>(env);
+  return new Engine<float>(env);
+}
+
+}  // namespace fpeps

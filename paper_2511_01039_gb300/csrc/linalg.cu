@@ -1,0 +1,528 @@
+// Randomized-SVD building blocks (Sec. IV; Halko et al. 2011, Example 1.6):
+// the Gaussian sketch Omega, FP64 Gram matrices, Cholesky QR, the one-sided
+// Jacobi SVD of small matrices, norms and layout helpers.
+//
+// Gaussian sketch: Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, layer)
+// with counter (i >> 1, j, site | stage << 16, row | env << 16); the word pair
+// (x0,x1) for even i and (x2,x3) for odd i gives u = ((x >> 11) + 0.5) 2^-53
+// and z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller). i is the flat row index of
+// the sketched space in C order of its (bond, bundle) legs.
+//
+// One-sided Jacobi SVD: Hestenes' method with the cyclic round-robin ordering;
+// each rotation makes two columns orthogonal (Demmel and Veselic 1992).
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace fpeps {
+namespace {
+
+constexpr uint64_t PH_M0 = 0xD2E7470EE14C6C93ull, PH_M1 = 0xCA5A826395121157ull;
+constexpr uint64_t PH_W0 = 0x9E3779B97F4A7C15ull, PH_W1 = 0xBB67AE8584CAA73Bull;
+
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(PH_M0, c[0]), lo0 = PH_M0 * c[0];
+    uint64_t hi1 = __umul64hi(PH_M1, c[2]), lo1 = PH_M1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += PH_W0; k1 += PH_W1;
+  }
+}
+
+__device__ __forceinline__ double u53(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1.0p-53; }
+
+// memory position pos = hi * lo_dim + lo within a column; canonical flat index
+// i = lo * hi_dim + hi when swap != 0, else i = pos.
+template <class T>
+__global__ void k_sketch(T* out, int64_t n_rows, int64_t k, int64_t ld, int64_t hi_dim, int64_t lo_dim, int swap,
+                         uint64_t seed, uint64_t layer, uint64_t w2, uint64_t w3) {
+  const int64_t n = n_rows * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / n_rows, pos = e % n_rows;
+    int64_t i = swap ? (pos % lo_dim) * hi_dim + pos / lo_dim : pos;
+    uint64_t c[4] = {(uint64_t)i >> 1, (uint64_t)j, w2, w3};
+    philox4x64(c, seed, layer);
+    uint64_t a = (i & 1) ? c[2] : c[0];
+    uint64_t b = (i & 1) ? c[3] : c[1];
+    double z = sqrt(-2.0 * log(u53(a))) * cospi(2.0 * u53(b));
+    out[j * ld + pos] = (T)z;
+  }
+}
+
+// G[i][j] += sum_r Y[i*ld + r] * Y[j*ld + r] over one row chunk; 32x32 tile per block.
+template <class T>
+__global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Y, int64_t m, int64_t k, int64_t ld,
+                                              int64_t chunk, double* G) {
+  __shared__ double si[32][33];
+  __shared__ double sj[32][33];
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (tj < ti) return;   // upper tiles only, mirrored at the end
+  const int64_t r0 = blockIdx.z * chunk, r1 = min(m, r0 + chunk);
+  const int tid = threadIdx.x;
+  const int li = tid / 8, lj = (tid % 8) * 4;   // each thread: 1 row x 4 cols of the tile
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t rb = r0; rb < r1; rb += 32) {
+    for (int e = tid; e < 32 * 32; e += 256) {
+      int c = e / 32, rr = e % 32;
+      int64_t r = rb + rr;
+      int64_t ci = (int64_t)ti * 32 + c, cj = (int64_t)tj * 32 + c;
+      si[c][rr] = (r < r1 && ci < k) ? (double)Y[ci * ld + r] : 0.0;
+      sj[c][rr] = (r < r1 && cj < k) ? (double)Y[cj * ld + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      double a = si[li][rr];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(a, sj[lj + q][rr], acc[q]);
+    }
+    __syncthreads();
+  }
+  int64_t gi = (int64_t)ti * 32 + li;
+  if (gi >= k) return;
+  for (int q = 0; q < 4; ++q) {
+    int64_t gj = (int64_t)tj * 32 + lj + q;
+    if (gj >= k || gj < gi) continue;
+    atomicAdd(&G[gi * k + gj], acc[q]);
+  }
+}
+
+__global__ void k_mirror_upper(double* G, int k) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = e / k, j = e % k;
+    if (j < i) G[e] = G[(int64_t)j * k + i];
+  }
+}
+
+// In-place Cholesky G = R^T R (R upper, row-major), one block. info = 1 when a
+// pivot is not positive or falls below tol * max diag (numerical rank loss).
+__global__ void __launch_bounds__(1024) k_cholesky(double* G, int k, double tol, int* info) {
+  __shared__ double piv_s;
+  __shared__ double dmax_s;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double dm = 0;
+    for (int i = 0; i < k; ++i) dm = fmax(dm, G[(int64_t)i * k + i]);
+    dmax_s = dm;
+    bad = !(dm > 0) || !isfinite(dm);
+  }
+  __syncthreads();
+  if (bad) { if (tid == 0) info[0] = 1; return; }
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      double d = G[(int64_t)j * k + j];
+      if (!(d > tol * dmax_s) || !isfinite(d)) bad = 1;
+      piv_s = sqrt(fmax(d, 0.0));
+      G[(int64_t)j * k + j] = piv_s;
+    }
+    __syncthreads();
+    if (bad) { if (tid == 0) info[0] = 1; return; }
+    const double piv = piv_s;
+    for (int c = j + 1 + tid; c < k; c += blockDim.x) G[(int64_t)j * k + c] /= piv;
+    __syncthreads();
+    const int n = k - j - 1;
+    // trailing update of the upper triangle: G[i][c] -= R[j][i] R[j][c], i <= c
+    for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
+      int i = j + 1 + (int)(e / n), c = j + 1 + (int)(e % n);
+      if (c >= i) G[(int64_t)i * k + c] -= G[(int64_t)j * k + i] * G[(int64_t)j * k + c];
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)k * k; e += blockDim.x) {
+    int i = e / k, c = e % k;
+    if (c < i) G[e] = 0.0;
+  }
+  if (tid == 0) info[0] = 0;
+}
+
+// Rinv = R^{-1} for upper-triangular R (row-major); column j solved by thread j.
+__global__ void k_tri_inverse(const double* R, int k, double* Rinv) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      if (i <= j) {
+        for (int l = i + 1; l <= j; ++l) s -= R[(int64_t)i * k + l] * Rinv[(int64_t)l * k + j];
+        s /= R[(int64_t)i * k + i];
+      } else {
+        s = 0.0;
+      }
+      Rinv[(int64_t)i * k + j] = s;
+    }
+  }
+}
+
+// One round of the one-sided Jacobi method on the columns of M (col-major,
+// k x k) with the accumulated right rotations in V. Pairs of the round-robin
+// schedule: player positions 0..kk-1 (kk even), position 0 fixed.
+__device__ __forceinline__ int rr_player(int pos, int round, int kk) {
+  if (pos == 0) return 0;
+  return 1 + ((pos - 1 + round) % (kk - 1));
+}
+
+__global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k, int max_sweeps, double eps,
+                                                      int* info) {
+  const int kk = (k % 2) ? k + 1 : k;   // dummy column k when odd
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+  __shared__ int rotated;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) V[e] = ((e / k) == (e % k)) ? 1.0 : 0.0;
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pr = warp; pr < kk / 2; pr += nwarp) {
+        int a = rr_player(pr, round, kk), b = rr_player(kk - 1 - pr, round, kk);
+        int p = min(a, b), q = max(a, b);
+        if (q >= k) continue;
+        double* mp = M + (int64_t)p * k;
+        double* mq = M + (int64_t)q * k;
+        double al = 0, be = 0, ga = 0;
+        for (int i = lane; i < k; i += 32) {
+          double x = mp[i], y = mq[i];
+          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+        }
+        for (int o = 16; o; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (fabs(ga) <= eps * sqrt(al * be) || ga == 0.0) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int i = lane; i < k; i += 32) {
+          double x = mp[i], y = mq[i];
+          mp[i] = c * x - s * y;
+          mq[i] = s * x + c * y;
+          double vx = V[(int64_t)p * k + i], vy = V[(int64_t)q * k + i];
+          V[(int64_t)p * k + i] = c * vx - s * vy;
+          V[(int64_t)q * k + i] = s * vx + c * vy;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) info[0] = (sweep >= max_sweeps) ? 2 : 0;
+}
+
+// sigma_j = |m_j|, U_j = m_j / sigma_j (0 when sigma_j == 0), written in
+// descending order of sigma (ties by index): sigma[rank], U[:, rank],
+// order[rank] = original column.
+__global__ void k_svd_finish(const double* M, int k, double* U, double* sigma, int* order) {
+  __shared__ double sig[1024];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0;
+    for (int i = 0; i < k; ++i) s = fma(M[(int64_t)j * k + i], M[(int64_t)j * k + i], s);
+    sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    int rank = 0;
+    for (int i = 0; i < k; ++i) rank += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
+    order[rank] = j;
+    sigma[rank] = sig[j];
+    double inv = sig[j] > 0 ? 1.0 / sig[j] : 0.0;
+    for (int i = 0; i < k; ++i) U[(int64_t)rank * k + i] = M[(int64_t)j * k + i] * inv;
+  }
+}
+
+template <class T, class S>
+__global__ void k_convert(const S* in, T* out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)in[e];
+}
+
+template <class T>
+__global__ void k_sumsq(const T* x, int64_t n, double* out) {
+  double s = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)x[e];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if (threadIdx.x % 32 == 0) ws[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < blockDim.x / 32 ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+__global__ void k_sqrt1(double* x) { x[0] = sqrt(x[0]); }
+
+template <class T>
+__global__ void k_scale_inv(T* x, int64_t n, const double* nrm) {
+  const double inv = 1.0 / nrm[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] = (T)((double)x[e] * inv);
+}
+
+template <class T>
+__global__ void k_permute3(const T* in, T* out, int64_t d0, int64_t d1, int64_t d2, int p0, int p1, int p2) {
+  // out dims are (d[p0], d[p1], d[p2]); in is [d0][d1][d2]
+  const int64_t n = d0 * d1 * d2;
+  int64_t d[3] = {d0, d1, d2};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o2 = e % d[p2], o1 = (e / d[p2]) % d[p1], o0 = e / (d[p2] * d[p1]);
+    int64_t idx[3];
+    idx[p0] = o0; idx[p1] = o1; idx[p2] = o2;
+    out[e] = in[(idx[0] * d1 + idx[1]) * d2 + idx[2]];
+  }
+}
+
+template <class T>
+__global__ void k_fill(T* x, int64_t n, T v) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) x[e] = v;
+}
+
+template <class T>
+__global__ void k_finite(const T* x, int64_t n, int* flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite((double)x[e])) flag[0] = 1;
+}
+
+
+// ---- small helpers used by the engine -------------------------------------
+// s_j = +1 if sum_i X(i, j) >= 0 else -1 (singular-vector sign gauge); one block per column
+template <class T>
+__global__ void k_col_signs(const T* X, int64_t m, int64_t ld, double* sgn) {
+  const int j = blockIdx.x;
+  double s = 0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += (double)X[(int64_t)j * ld + i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if (threadIdx.x % 32 == 0) ws[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += ws[w];
+    sgn[j] = t < 0 ? -1.0 : 1.0;
+  }
+}
+
+template <class T>
+__global__ void k_scale_cols(T* X, int64_t m, int n, int64_t ld, const double* sc) {
+  const int64_t tot = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / m, i = e % m;
+    X[j * ld + i] = (T)((double)X[j * ld + i] * sc[j]);
+  }
+}
+
+__global__ void k_mul_vec(const double* a, const double* b, double* out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] * b[i];
+}
+
+__global__ void k_gather_cols(const double* V, const int* order, int k, double* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(e / k), i = (int)(e % k);
+    out[e] = V[(int64_t)order[r] * k + i];
+  }
+}
+
+template <class T>
+__global__ void k_set_identity(T* X, int64_t m, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * n; e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = (e / m == e % m) ? T(1) : T(0);
+}
+
+// SVQB factors from the Gram matrix G (k x k): d_i = G_ii^{-1/2}, scaled Gram
+// D G D = V diag(lam) V^T (one-sided Jacobi of a symmetric PSD matrix gives its
+// eigenvectors as right singular vectors), kept where lam_r > 1e-15 lam_0.
+//   Bt (col-major)  = D V diag(lam^{-1/2})        Y Bt = Q
+//   Rq (row-major)  = diag(lam^{1/2}) V^T D^{-1}  Y ~= Q Rq
+__global__ void k_svqb_scale(const double* G, int k, double* d, double* Gs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), j = (int)(e % k);
+    double gi = G[(int64_t)i * k + i], gj = G[(int64_t)j * k + j];
+    double di = gi > 0 ? rsqrt(gi) : 0.0, dj = gj > 0 ? rsqrt(gj) : 0.0;
+    Gs[e] = G[e] * di * dj;
+    if (j == 0) d[i] = di;
+  }
+}
+
+__global__ void k_svqb_factors(const double* V, const double* lam, const double* d, int k, double* Bt, double* Rq) {
+  const double lmax = lam[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(e / k), i = (int)(e % k);   // column r, row i
+    double l = lam[r];
+    bool keep = l > 1e-15 * lmax && lmax > 0;
+    double v = V[(int64_t)r * k + i];
+    Bt[(int64_t)r * k + i] = keep ? d[i] * v / sqrt(l) : 0.0;
+    Rq[(int64_t)r * k + i] = (keep && d[i] > 0) ? sqrt(l) * v / d[i] : 0.0;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g));
+}
+
+}  // namespace
+
+template <class T>
+void gaussian_sketch(cudaStream_t s, T* out, int64_t n_rows, int64_t k, int64_t ld, const int64_t* perm_div,
+                     uint64_t seed, uint64_t layer, uint64_t w2, uint64_t w3) {
+  int64_t hi = perm_div ? perm_div[0] : 1, lo = perm_div ? perm_div[1] : n_rows;
+  k_sketch<T><<<grid_for(n_rows * k), 256, 0, s>>>(out, n_rows, k, ld, hi, lo, perm_div ? 1 : 0, seed, layer, w2, w3);
+  FP_LAUNCH();
+}
+
+template <class T>
+void gram_f64(cudaStream_t s, const T* Y, int64_t m, int64_t k, int64_t ld, double* G) {
+  FP_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * k * k, s));
+  int tiles = (int)((k + 31) / 32);
+  int64_t target_blocks = 152 * 8;
+  int64_t tri = (int64_t)tiles * (tiles + 1) / 2;
+  int64_t nchunk = (target_blocks + tri - 1) / tri;
+  int64_t chunk = (m + nchunk - 1) / nchunk;
+  chunk = ((chunk + 31) / 32) * 32;
+  if (chunk < 32) chunk = 32;
+  nchunk = (m + chunk - 1) / chunk;
+  if (nchunk < 1) nchunk = 1;
+  dim3 grid(tiles, tiles, (unsigned)nchunk);
+  k_gram<T><<<grid, 256, 0, s>>>(Y, m, k, ld, chunk, G);
+  FP_LAUNCH();
+  k_mirror_upper<<<grid_for(k * k), 256, 0, s>>>(G, (int)k);
+  FP_LAUNCH();
+}
+
+void cholesky_upper_f64(cudaStream_t s, double* G, int k, int* info) {
+  k_cholesky<<<1, 1024, 0, s>>>(G, k, 1e-13, info);
+  FP_LAUNCH();
+}
+
+void tri_inverse_upper_f64(cudaStream_t s, const double* R, int k, double* Rinv) {
+  k_tri_inverse<<<(k + 127) / 128, 128, 0, s>>>(R, k, Rinv);
+  FP_LAUNCH();
+}
+
+void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma, double* V, int* order, int* info) {
+  FP_CHECK(k <= 1024, FPEPS_ERR_UNSUPPORTED, "svd: k > 1024");
+  k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15, info);
+  FP_LAUNCH();
+  k_svd_finish<<<1, 1024, 0, s>>>(Mat, k, U, sigma, order);
+  FP_LAUNCH();
+}
+
+template <class T>
+void convert_f64(cudaStream_t s, const double* in, T* out, int64_t n) {
+  k_convert<T, double><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  FP_LAUNCH();
+}
+template <class T>
+void to_f64(cudaStream_t s, const T* in, double* out, int64_t n) {
+  k_convert<double, T><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  FP_LAUNCH();
+}
+
+template <class T>
+void frob_norm_f64(cudaStream_t s, const T* x, int64_t n, double* out) {
+  FP_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+  k_sumsq<T><<<grid_for(n), 256, 0, s>>>(x, n, out);
+  FP_LAUNCH();
+  k_sqrt1<<<1, 1, 0, s>>>(out);
+  FP_LAUNCH();
+}
+
+template <class T>
+void scale_by_inv(cudaStream_t s, T* x, int64_t n, const double* nrm) {
+  k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(x, n, nrm);
+  FP_LAUNCH();
+}
+
+template <class T>
+void permute3(cudaStream_t s, const T* in, T* out, int64_t d0, int64_t d1, int64_t d2, int p0, int p1, int p2) {
+  k_permute3<T><<<grid_for(d0 * d1 * d2), 256, 0, s>>>(in, out, d0, d1, d2, p0, p1, p2);
+  FP_LAUNCH();
+}
+
+template <class T>
+void fill(cudaStream_t s, T* x, int64_t n, T v) {
+  if (n <= 0) return;
+  k_fill<T><<<grid_for(n), 256, 0, s>>>(x, n, v);
+  FP_LAUNCH();
+}
+
+template <class T>
+void check_finite(cudaStream_t s, const T* x, int64_t n, int* flag) {
+  if (n <= 0) return;
+  k_finite<T><<<grid_for(n), 256, 0, s>>>(x, n, flag);
+  FP_LAUNCH();
+}
+
+
+template <class T>
+void col_signs(cudaStream_t s, const T* X, int64_t m, int n, int64_t ld, double* sgn) {
+  if (n <= 0) return;
+  k_col_signs<T><<<n, 256, 0, s>>>(X, m, ld, sgn);
+  FP_LAUNCH();
+}
+template <class T>
+void scale_cols(cudaStream_t s, T* X, int64_t m, int n, int64_t ld, const double* sc) {
+  if (n <= 0 || m <= 0) return;
+  k_scale_cols<T><<<grid_for(m * n), 256, 0, s>>>(X, m, n, ld, sc);
+  FP_LAUNCH();
+}
+void mul_vec(cudaStream_t s, const double* a, const double* b, double* out, int n) {
+  k_mul_vec<<<(n + 255) / 256, 256, 0, s>>>(a, b, out, n);
+  FP_LAUNCH();
+}
+void gather_cols_f64(cudaStream_t s, const double* V, const int* order, int k, double* out) {
+  k_gather_cols<<<grid_for((int64_t)k * k), 256, 0, s>>>(V, order, k, out);
+  FP_LAUNCH();
+}
+template <class T>
+void set_identity(cudaStream_t s, T* X, int64_t m, int n) {
+  k_set_identity<T><<<grid_for(m * n), 256, 0, s>>>(X, m, n);
+  FP_LAUNCH();
+}
+template <class T>
+void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst) {
+  FP_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, s));
+}
+void svqb_factors(cudaStream_t s, const double* G, int k, double* work, double* Bt, double* Rq, int* info) {
+  double* d = work;
+  double* Gs = d + k;
+  double* U = Gs + (int64_t)k * k;
+  double* V = U + (int64_t)k * k;
+  double* Vs = V + (int64_t)k * k;
+  double* lam = Vs + (int64_t)k * k;
+  int* order = (int*)(lam + k);
+  k_svqb_scale<<<grid_for((int64_t)k * k), 256, 0, s>>>(G, k, d, Gs);
+  FP_LAUNCH();
+  svd_jacobi_f64(s, Gs, k, U, lam, V, order, info);
+  gather_cols_f64(s, V, order, k, Vs);
+  k_svqb_factors<<<grid_for((int64_t)k * k), 256, 0, s>>>(Vs, lam, d, k, Bt, Rq);
+  FP_LAUNCH();
+}
+
+#define INST(T)                                                                                              \
+  template void gaussian_sketch<T>(cudaStream_t, T*, int64_t, int64_t, int64_t, const int64_t*, uint64_t,    \
+                                   uint64_t, uint64_t, uint64_t);                                            \
+  template void gram_f64<T>(cudaStream_t, const T*, int64_t, int64_t, int64_t, double*);                      \
+  template void convert_f64<T>(cudaStream_t, const double*, T*, int64_t);                                    \
+  template void to_f64<T>(cudaStream_t, const T*, double*, int64_t);                                          \
+  template void frob_norm_f64<T>(cudaStream_t, const T*, int64_t, double*);                                  \
+  template void scale_by_inv<T>(cudaStream_t, T*, int64_t, const double*);                                   \
+  template void permute3<T>(cudaStream_t, const T*, T*, int64_t, int64_t, int64_t, int, int, int);            \
+  template void fill<T>(cudaStream_t, T*, int64_t, T);                                                        \
+  template void check_finite<T>(cudaStream_t, const T*, int64_t, int*);                                      \
+  template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, double*);                         \
+  template void scale_cols<T>(cudaStream_t, T*, int64_t, int, int64_t, const double*);                        \
+  template void set_identity<T>(cudaStream_t, T*, int64_t, int);                                              \
+  template void copy_cols<T>(cudaStream_t, const T*, int64_t, int, T*);
+INST(float)
+INST(double)
+template void fill<int>(cudaStream_t, int*, int64_t, int);
+
+}  // namespace fpeps

@@ -1,0 +1,247 @@
+// The site sandwich C = A (x) W (x) A applied to blocks of vectors (Sec. III).
+//
+// The paper computes and stores the sandwich but advises against fusing the
+// PEPO indices, because PEPO tensors of local Hamiltonians have structure
+// beyond quantum-number conservation. Here the PEPO enters channel by channel:
+// only the nonzero (l_w,u_w,r_w,d_w) blocks W_ch[p,p'] are visited, with the
+// ket and the PEPO block pre-multiplied (A . W_ch), and the bra applied once
+// per output (v_w, z_w) pair. C itself is never materialised.
+//
+// A block of the input, I[X][Y] with X = (x, x_w, x'), Y = (y, y_w, y')
+// (bra fastest), maps to O[V][Z] with V = (v, v_w, v'), Z = (z, z_w, z'):
+//   acc[x',y',v,z,q]   = sum_{ch in (v_w,z_w)} sum_{x,y} I[(x,x_w,x'),(y,y_w,y')] AW_ch[x,y,v,z,q]
+//   O[(v,v_w,v'),(z,z_w,z')] = sum_{x',y',q} acc[x',y',v,z,q] A[x',y',v',z',q]
+#include "common.cuh"
+
+namespace fpeps {
+namespace {
+
+template <class T>
+__global__ void k_pepo_scan(const T* W, int n_ch, int pp, int* flags) {
+  int ch = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ch >= n_ch) return;
+  int f = 0;
+  for (int i = 0; i < pp; ++i) f |= (W[(int64_t)ch * pp + i] != T(0));
+  flags[ch] = f;
+}
+
+// index of a 4-leg site tensor element from role-ordered leg values
+__device__ __forceinline__ int64_t leg_index(const int* dims, const int* roles, const int* vals) {
+  int l[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) l[roles[r]] = vals[r];
+  return (((int64_t)l[0] * dims[1] + l[1]) * dims[2] + l[2]) * dims[3] + l[3];
+}
+
+struct PrepArgs {
+  int dA[5];
+  int dW[6];
+  int roles[4];
+};
+
+template <class T>
+__global__ void k_prepare_ar(const T* A, PrepArgs a, T* ar) {
+  const int nx = a.dA[a.roles[0]], ny = a.dA[a.roles[1]], nv = a.dA[a.roles[2]], nz = a.dA[a.roles[3]];
+  const int p = a.dA[4];
+  int64_t n = (int64_t)nx * ny * nv * nz * p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e;
+    int q = r % p; r /= p;
+    int z = r % nz; r /= nz;
+    int v = r % nv; r /= nv;
+    int y = r % ny; r /= ny;
+    int x = (int)r;
+    int vals[4] = {x, y, v, z};
+    ar[e] = A[leg_index(a.dA, a.roles, vals) * p + q];
+  }
+}
+
+template <class T>
+__global__ void k_prepare_aw(const T* ar, const T* W, PrepArgs a, const int* ch, int nch, T* aw) {
+  const int nx = a.dA[a.roles[0]], ny = a.dA[a.roles[1]], nv = a.dA[a.roles[2]], nz = a.dA[a.roles[3]];
+  const int p = a.dA[4];
+  const int64_t per = (int64_t)nx * ny * nv * nz * p;
+  const int64_t n = per * nch;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(e / per);
+    int64_t r = e % per;
+    int q = r % p;
+    int64_t base = r - q;   // element (x,y,v,z,0) of ar
+    int wv[4] = {ch[4 * c + 0], ch[4 * c + 1], ch[4 * c + 2], ch[4 * c + 3]};
+    int64_t wch = leg_index(a.dW, a.roles, wv) * p * p;   // W[l,u,r,d,:,:]
+    T s = T(0);
+    for (int pi = 0; pi < p; ++pi) s += ar[base + pi] * W[wch + (int64_t)pi * p + q];
+    aw[e] = s;
+  }
+}
+
+template <class T>
+__global__ void k_first_row(const T* A, PrepArgs a, const T* W, T* out) {
+  // T[L][Dn][R], L=(l,lw,l'), Dn=(d,dw,d'), R=(r,rw,r'); up legs have dimension 1
+  const int Dl = a.dA[0], Dr = a.dA[2], Dd = a.dA[3], p = a.dA[4];
+  const int wl = a.dW[0], wr = a.dW[2], wd = a.dW[3];
+  const int64_t nL = (int64_t)Dl * wl * Dl, nD = (int64_t)Dd * wd * Dd, nR = (int64_t)Dr * wr * Dr;
+  const int64_t n = nL * nD * nR;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t R = e % nR, Dn = (e / nR) % nD, L = e / (nR * nD);
+    int rb = R % Dr, rw = (R / Dr) % wr, rk = R / (Dr * wr);
+    int db = Dn % Dd, dw = (Dn / Dd) % wd, dk = Dn / (Dd * wd);
+    int lb = L % Dl, lw = (L / Dl) % wl, lk = L / (Dl * wl);
+    const T* ak = A + ((((int64_t)lk * 1 + 0) * Dr + rk) * Dd + dk) * p;
+    const T* ab = A + ((((int64_t)lb * 1 + 0) * Dr + rb) * Dd + db) * p;
+    const T* w = W + ((((int64_t)lw * 1 + 0) * wr + rw) * wd + dw) * p * p;
+    T s = T(0);
+    for (int i = 0; i < p; ++i) {
+      T t = T(0);
+      for (int j = 0; j < p; ++j) t += w[i * p + j] * ab[j];
+      s += ak[i] * t;
+    }
+    out[e] = s;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, const T* __restrict__ in, int64_t i_t,
+                                                  int64_t i_k, int64_t i_X, int64_t i_Y, T* __restrict__ out,
+                                                  int64_t o_t, int64_t o_k, int64_t o_V, int64_t o_Z) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int nx = o.nx, ny = o.ny, nv = o.nv, nz = o.nz, p = o.p;
+  const int nsl = nx * nx * ny * ny;          // I slice [x][x'][y][y']
+  const int nacc = nx * ny * nv * nz * p;     // acc [x'][y'][v][z][q] and ar/aw [x][y][v][z][q]
+  T* isl = sm;
+  T* acc = isl + nsl;
+  T* ar = acc + nacc;
+  T* aw = ar + nacc;
+  const T* AW = static_cast<const T*>(o.d_aw);
+  const T* AR = static_cast<const T*>(o.d_ar);
+
+  const int64_t blk = blockIdx.x;
+  const int64_t t = blk / nk, k = blk % nk;
+  const T* I = in + t * i_t + k * i_k;
+  T* O = out + t * o_t + k * o_k;
+  const int tid = threadIdx.x;
+
+  for (int e = tid; e < nacc; e += blockDim.x) ar[e] = AR[e];
+
+  for (int vw = 0; vw < o.nvw; ++vw) {
+    for (int zw = 0; zw < o.nzw; ++zw) {
+      const int pair = vw * o.nzw + zw;
+      for (int e = tid; e < nacc; e += blockDim.x) acc[e] = T(0);
+      const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
+      for (int c = c0; c < c1; ++c) {
+        const int xw = o.d_ch[4 * c + 0], yw = o.d_ch[4 * c + 1];
+        __syncthreads();
+        for (int e = tid; e < nsl; e += blockDim.x) {
+          int yp = e % ny, y = (e / ny) % ny, xp = (e / (ny * ny)) % nx, x = e / (ny * ny * nx);
+          int64_t X = ((int64_t)x * o.nxw + xw) * nx + xp;
+          int64_t Y = ((int64_t)y * o.nyw + yw) * ny + yp;
+          isl[e] = I[X * i_X + Y * i_Y];
+        }
+        const T* awc = AW + (int64_t)c * nacc;
+        for (int e = tid; e < nacc; e += blockDim.x) aw[e] = awc[e];
+        __syncthreads();
+        // acc[x'][y'][v][z][q] += sum_{x,y} isl[x][x'][y][y'] aw[x][y][v][z][q]
+        const int nvzq = nv * nz * p;
+        for (int e = tid; e < nacc; e += blockDim.x) {
+          int vzq = e % nvzq, yp = (e / nvzq) % ny, xp = e / (nvzq * ny);
+          T s = T(0);
+          for (int x = 0; x < nx; ++x)
+            for (int y = 0; y < ny; ++y)
+              s += isl[((x * nx + xp) * ny + y) * ny + yp] * aw[(x * ny + y) * nvzq + vzq];
+          acc[e] += s;
+        }
+      }
+      __syncthreads();
+      // O[(v,vw,v'),(z,zw,z')] = sum_{x',y',q} acc[x'][y'][v][z][q] ar[x'][y'][v'][z'][q]
+      const int nout = nv * nv * nz * nz;
+      for (int e = tid; e < nout; e += blockDim.x) {
+        int zp = e % nz, z = (e / nz) % nz, vp = (e / (nz * nz)) % nv, v = e / (nz * nz * nv);
+        T s = T(0);
+        for (int xp = 0; xp < nx; ++xp)
+          for (int yp = 0; yp < ny; ++yp) {
+            const T* ac = acc + ((xp * ny + yp) * nv + v) * nz * p + z * p;
+            const T* br = ar + ((xp * ny + yp) * nv + vp) * nz * p + zp * p;
+            for (int q = 0; q < p; ++q) s += ac[q] * br[q];
+          }
+        int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp;
+        int64_t Z = ((int64_t)z * o.nzw + zw) * nz + zp;
+        O[V * o_V + Z * o_Z] = s;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g));
+}
+
+}  // namespace
+
+template <class T>
+void pepo_scan(cudaStream_t s, const T* W, const int dW[6], int* d_flags) {
+  int nch = dW[0] * dW[1] * dW[2] * dW[3];
+  k_pepo_scan<T><<<(nch + 127) / 128, 128, 0, s>>>(W, nch, dW[4] * dW[5], d_flags);
+  FP_LAUNCH();
+}
+
+template <class T>
+void sandwich_prepare(cudaStream_t s, const T* A, const int dA[5], const T* W, const int dW[6], const int roles[4],
+                      const int* d_ch, int nch, T* d_aw, T* d_ar) {
+  PrepArgs a;
+  for (int i = 0; i < 5; ++i) a.dA[i] = dA[i];
+  for (int i = 0; i < 6; ++i) a.dW[i] = dW[i];
+  for (int i = 0; i < 4; ++i) a.roles[i] = roles[i];
+  int64_t per = (int64_t)dA[roles[0]] * dA[roles[1]] * dA[roles[2]] * dA[roles[3]] * dA[4];
+  k_prepare_ar<T><<<grid_for(per), 256, 0, s>>>(A, a, d_ar);
+  FP_LAUNCH();
+  if (nch > 0) {
+    k_prepare_aw<T><<<grid_for(per * nch), 256, 0, s>>>(d_ar, W, a, d_ch, nch, d_aw);
+    FP_LAUNCH();
+  }
+}
+
+template <class T>
+void first_row_tensor(cudaStream_t s, const T* A, const int dA[5], const T* W, const int dW[6], T* out) {
+  PrepArgs a;
+  for (int i = 0; i < 5; ++i) a.dA[i] = dA[i];
+  for (int i = 0; i < 6; ++i) a.dW[i] = dW[i];
+  int64_t n = (int64_t)dA[0] * dW[0] * dA[0] * dA[3] * dW[3] * dA[3] * dA[2] * dW[2] * dA[2];
+  k_first_row<T><<<grid_for(n), 256, 0, s>>>(A, a, W, out);
+  FP_LAUNCH();
+}
+
+template <class T>
+void sandwich_apply(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const T* in, int64_t i_t,
+                    int64_t i_k, int64_t i_X, int64_t i_Y, T* out, int64_t o_t, int64_t o_k, int64_t o_V,
+                    int64_t o_Z) {
+  if (nt <= 0 || nk <= 0) return;
+  size_t nsl = (size_t)o.nx * o.nx * o.ny * o.ny;
+  size_t nacc = (size_t)o.nx * o.ny * o.nv * o.nz * o.p;
+  size_t smem = (nsl + 3 * nacc) * sizeof(T);
+  FP_CHECK(smem <= 200 * 1024, FPEPS_ERR_UNSUPPORTED, "sandwich: site too large for shared memory");
+  static bool attr_set[2] = {false, false};
+  int idx = sizeof(T) == 8 ? 1 : 0;
+  if (!attr_set[idx]) {
+    FP_CUDA(cudaFuncSetAttribute(k_sandwich<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set[idx] = true;
+  }
+  int64_t nblk = nt * nk;
+  FP_CHECK(nblk < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "sandwich: too many blocks");
+  k_sandwich<T><<<(unsigned)nblk, 256, smem, s>>>(o, nk, in, i_t, i_k, i_X, i_Y, out, o_t, o_k, o_V, o_Z);
+  FP_LAUNCH();
+}
+
+#define INST(T)                                                                                                   \
+  template void pepo_scan<T>(cudaStream_t, const T*, const int[6], int*);                                        \
+  template void sandwich_prepare<T>(cudaStream_t, const T*, const int[5], const T*, const int[6], const int[4],  \
+                                    const int*, int, T*, T*);                                                     \
+  template void first_row_tensor<T>(cudaStream_t, const T*, const int[5], const T*, const int[6], T*);          \
+  template void sandwich_apply<T>(cudaStream_t, const SandOrient&, int64_t, int64_t, const T*, int64_t, int64_t, \
+                                  int64_t, int64_t, T*, int64_t, int64_t, int64_t, int64_t);
+INST(float)
+INST(double)
+
+}  // namespace fpeps

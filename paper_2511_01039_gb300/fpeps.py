@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libfpeps (include/fpeps.h): argument marshalling only.
+
+Every step of the contraction runs in the library's CUDA kernels; this module
+only converts Python/PyTorch arguments to the C ABI. It raises if the native
+library is missing: there is no fallback implementation.
+
+PyTorch supplies device memory (through the allocator callback, backed by the
+caching allocator) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libfpeps.so")
+
+F64, F32, TF32X3, BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"f64": F64, "f32": F32, "tf32x3": TF32X3, "bf16x3": BF16X3}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_OOM", 4: "ERR_CUDA", 5: "ERR_NUMERIC", 6: "ERR_TIMEOUT",
+          7: "ERR_UNSUPPORTED"}
+
+
+class fpeps_config(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32), ("D", C.c_int32), ("p", C.c_int32), ("w", C.c_int32),
+                ("chi", C.c_int32), ("prec", C.c_int), ("seed", C.c_uint64), ("symmetry", C.c_int32),
+                ("n_envs", C.c_int32)]
+
+
+class fpeps_rsvd_params(C.Structure):
+    _fields_ = [("oversample", C.c_int32), ("power_iters", C.c_int32), ("chi_tilde", C.c_int32),
+                ("n_fit", C.c_int32), ("exact_svd", C.c_int32)]
+
+
+class fpeps_stats(C.Structure):
+    _fields_ = [("seconds", C.c_double), ("alg_flops", C.c_double), ("log_scale", C.c_double),
+                ("trunc_err_est", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class fpeps_allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+class FpepsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# symbol name -> (restype, argtypes)
+SIGNATURES = {
+    "fpeps_env_create": (C.c_int, [C.POINTER(fpeps_config), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                   C.c_void_p, C.POINTER(fpeps_allocator), C.POINTER(C.c_void_p)]),
+    "fpeps_absorb_row": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "fpeps_compress_rsvd": (C.c_int, [C.c_void_p, C.POINTER(fpeps_rsvd_params), C.POINTER(fpeps_stats)]),
+    "fpeps_sweep_value": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "fpeps_contract_norm": (C.c_int, [C.c_void_p, C.POINTER(fpeps_rsvd_params), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int32)]),
+    "fpeps_expect": (C.c_int, [C.c_void_p, C.POINTER(fpeps_rsvd_params), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "fpeps_export_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "fpeps_import_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32, C.c_int32]),
+    "fpeps_last_error": (C.c_char_p, [C.c_void_p]),
+    "fpeps_env_destroy": (None, [C.c_void_p]),
+    "fpeps_boundary_shape": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32)]),
+    "fpeps_bond_spectrum": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int32)]),
+    "fpeps_apply_theta": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                    C.c_void_p]),
+    "fpeps_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libfpeps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FpepsError(-1, f"native library missing: {LIB_PATH} (run __graft_entry__.build())")
+        _lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _check(env, st):
+    if st != 0:
+        msg = lib().fpeps_last_error(env).decode() if env else ""
+        raise FpepsError(st, msg)
+
+
+class TorchAllocator:
+    """fpeps_allocator backed by torch's caching allocator (one uint8 tensor per block)."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self._a = ALLOC_FN(self._alloc)
+        self._f = FREE_FN(self._free)
+        self.struct = fpeps_allocator(None, self._a, self._f)
+
+    def _alloc(self, ctx, nbytes, stream):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except RuntimeError:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ctx, ptr, stream):
+        self.live.pop(ptr, None)
+
+
+# ------------------------------------------------------------------ same-name wrappers
+def fpeps_env_create(cfg: fpeps_config, peps, pepo, dtype_in: int, stream_handle: int, allocator=None):
+    """peps/pepo: device pointers (int) or torch tensors; returns the env handle (c_void_p)."""
+    out = C.c_void_p()
+    pp = peps.data_ptr() if hasattr(peps, "data_ptr") else peps
+    wp = (pepo.data_ptr() if hasattr(pepo, "data_ptr") else pepo) if pepo is not None else None
+    al = C.byref(allocator.struct) if allocator is not None else None
+    st = lib().fpeps_env_create(C.byref(cfg), pp, wp, None, dtype_in, stream_handle, al, C.byref(out))
+    _check(None, st)
+    return out
+
+
+def fpeps_absorb_row(env, row: int, layer: int):
+    _check(env, lib().fpeps_absorb_row(env, row, layer))
+
+
+def fpeps_compress_rsvd(env, params: fpeps_rsvd_params):
+    st = fpeps_stats()
+    _check(env, lib().fpeps_compress_rsvd(env, C.byref(params), C.byref(st)))
+    return st
+
+
+def fpeps_sweep_value(env):
+    la, sg = C.c_double(), C.c_int32()
+    _check(env, lib().fpeps_sweep_value(env, C.byref(la), C.byref(sg)))
+    return sg.value, la.value
+
+
+def fpeps_contract_norm(env, params: fpeps_rsvd_params):
+    la, sg = C.c_double(), C.c_int32()
+    _check(env, lib().fpeps_contract_norm(env, C.byref(params), C.byref(la), C.byref(sg)))
+    return sg.value, la.value
+
+
+def fpeps_expect(env, params: fpeps_rsvd_params):
+    v, la, sg = C.c_double(), C.c_double(), C.c_int32()
+    _check(env, lib().fpeps_expect(env, C.byref(params), C.byref(v), C.byref(la), C.byref(sg)))
+    return v.value, sg.value, la.value
+
+
+def fpeps_export_boundary(env) -> bytes:
+    n = C.c_size_t(0)
+    _check(env, lib().fpeps_export_boundary(env, None, C.byref(n)))
+    buf = (C.c_char * n.value)()
+    _check(env, lib().fpeps_export_boundary(env, buf, C.byref(n)))
+    return bytes(buf)
+
+
+def fpeps_import_boundary(env, blob: bytes, next_row: int, layer: int):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(env, lib().fpeps_import_boundary(env, buf, len(blob), next_row, layer))
+
+
+def fpeps_last_error(env) -> str:
+    return lib().fpeps_last_error(env).decode()
+
+
+def fpeps_env_destroy(env):
+    lib().fpeps_env_destroy(env)
+
+
+def fpeps_boundary_shape(env, c: int):
+    a, b, d = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(env, lib().fpeps_boundary_shape(env, c, C.byref(a), C.byref(b), C.byref(d)))
+    return a.value, b.value, d.value
+
+
+def fpeps_bond_spectrum(env, which: int, c: int):
+    n = C.c_int32(0)
+    _check(env, lib().fpeps_bond_spectrum(env, which, c, None, C.byref(n)))
+    arr = (C.c_double * max(n.value, 1))()
+    _check(env, lib().fpeps_bond_spectrum(env, which, c, arr, C.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def fpeps_apply_theta(env, c: int, el, x, dn: int, elem_bytes: int):
+    """Theta_c of the staged row on host vectors: el [a, t, L], x [k, t', R] -> y [k, a, dn] (numpy)."""
+    import numpy as np
+    dt = np.float64 if elem_bytes == 8 else np.float32
+    el = np.ascontiguousarray(el, dtype=dt)
+    x = np.ascontiguousarray(x, dtype=dt)
+    a, k = el.shape[0], x.shape[0]
+    y = np.zeros((k, a, dn), dtype=dt)
+    _check(env, lib().fpeps_apply_theta(env, c, a, el.ctypes.data, k, x.ctypes.data, y.ctypes.data))
+    return y
+
+
+def fpeps_version() -> str:
+    return lib().fpeps_version().decode()
+
+
+# ------------------------------------------------------------------ convenience
+class Env:
+    """An fpeps environment on the current CUDA device and stream.
+
+    peps / pepo: lists of lists of site tensors (numpy or torch), packed and copied
+    to the device once; ``prec`` one of 'f64', 'f32', 'tf32x3', 'bf16x3'.
+    """
+
+    def __init__(self, peps, pepo, *, D, p, w, chi, prec="f64", seed=0, stream=None, use_torch_allocator=True):
+        import numpy as np
+        import torch
+        self.torch = torch
+        Lx, Ly = len(peps), len(peps[0])
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream or torch.cuda.current_stream(self.dev)
+        dt = torch.float64
+        pk = torch.cat([torch.as_tensor(np.asarray(t), dtype=dt).reshape(-1) for row in peps for t in row]).to(self.dev)
+        wk = None
+        if pepo is not None:
+            wk = torch.cat([torch.as_tensor(np.asarray(t), dtype=dt).reshape(-1) for row in pepo for t in row]).to(self.dev)
+        self.cfg = fpeps_config(Lx, Ly, D, p, w, chi, PRECISIONS[prec], seed, 0, 1)
+        self.elem = 8 if prec == "f64" else 4
+        self.alloc = TorchAllocator(self.dev) if use_torch_allocator else None
+        torch.cuda.synchronize(self.dev)
+        self.h = fpeps_env_create(self.cfg, pk, wk, 0, self.stream.cuda_stream, self.alloc)
+        del pk, wk
+
+    def close(self):
+        if getattr(self, "h", None):
+            fpeps_env_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def norm(self, params):
+        return fpeps_contract_norm(self.h, params)
+
+    def expect(self, params):
+        return fpeps_expect(self.h, params)
+
+    def apply_theta(self, c, el, x, dn):
+        """One Theta_c application of the staged row (diagnostic): el [a,t,L], x [k,t',R] -> y [k,a,dn]."""
+        return fpeps_apply_theta(self.h, c, el, x, dn, self.elem)
+
+
+def params(oversample=10, power_iters=2, chi_tilde=0, n_fit=1, exact_svd=0) -> fpeps_rsvd_params:
+    return fpeps_rsvd_params(oversample, power_iters, chi_tilde, n_fit, int(exact_svd))

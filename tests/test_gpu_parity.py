@@ -1,0 +1,169 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: the FP64 path runs the oracle's algorithm in double precision and
+must agree to 1e-8 relative on <psi|O|psi> (the bar for the FP64 mode); the
+FP32 path is held to 1e-4 on the small lattices here (FP32 unit roundoff
+6e-8, amplified through ~O(10) chained factorisations and truncations).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import boundary as B
+from oracle import network as N
+from synth import lattice as L
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import torch
+    from paper_2511_01039_gb300 import fpeps
+    torch.cuda.set_device(0)
+    fpeps.lib()
+    return fpeps
+
+
+def _rel(a, b):
+    return abs(a / b - 1.0)
+
+
+def _env(fp, peps, pepo, *, D, w, chi, prec, seed):
+    return fp.Env(peps, pepo, D=D, p=4, w=w, chi=chi, prec=prec, seed=seed)
+
+
+@pytest.mark.parametrize("kind", ["identity", "dense2", "fsm2", "fsm4"])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_c1_3x3_exact_against_brute_force(fp, kind, prec, tol):
+    peps = L.random_peps(3, 3, 2, 4, seed=0)
+    if kind == "identity":
+        pepo, w = L.identity_pepo(3, 3, 4), 1
+    elif kind == "dense2":
+        pepo, w = L.dense_pepo(3, 3, 4, 2, seed=1), 2
+    elif kind == "fsm2":
+        pepo, w = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 0, seed=1)), 2
+    else:
+        pepo, w = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 2, seed=1)), 4
+    num, den = N.brute_force_expectation(peps, pepo)
+    env = _env(fp, peps, pepo, D=2, w=w, chi=16, prec=prec, seed=9)
+    prm = fp.params(oversample=10, power_iters=0, n_fit=1, exact_svd=1)
+    val, sn, ln = env.expect(prm)
+    sd, ld = env.norm(prm)
+    env.close()
+    assert _rel(sn * math.exp(ln), num) < tol
+    assert _rel(sd * math.exp(ld), den) < tol
+    assert _rel(val, num / den) < 2 * tol
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4)])
+@pytest.mark.parametrize("n_fit", [0, 1])
+def test_truncated_4x4_matches_oracle_algorithm(fp, prec, tol, n_fit):
+    """Truncated regime (chi=12 < exact bonds): same algorithm, same Omega, both sides."""
+    peps = L.random_peps(4, 4, 2, 4, seed=3)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=3))
+    prm_o = B.RsvdParams(oversample=6, power_iters=2, n_fit=n_fit)
+    sn_o, ln_o = B.contract(peps, pepo, 12, prm_o, seed=5, layer=1)
+    env = _env(fp, peps, pepo, D=2, w=4, chi=12, prec=prec, seed=5)
+    # operator sweep through the row-level ABI
+    for r in range(4):
+        fp.fpeps_absorb_row(env.h, r, 1)
+        if 0 < r < 3:
+            st = fp.fpeps_compress_rsvd(env.h, fp.params(6, 2, 0, n_fit, 0))
+            assert st.alg_flops > 0 and st.seconds > 0
+    sg, lg = fp.fpeps_sweep_value(env.h)
+    env.close()
+    assert sg == sn_o
+    assert abs(lg - ln_o) < tol
+
+
+def test_zip_spectrum_and_apply_theta_match_oracle(fp):
+    peps = L.random_peps(4, 4, 2, 4, seed=4)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=4))
+    T, _ = B.first_row_boundary(peps[0], pepo[0])
+    prm_o = B.RsvdParams(oversample=6, power_iters=2, n_fit=1)
+    res = B.absorb_row(T, peps[1], pepo[1], 12, prm_o, seed=5, layer=1, row=1)
+    env = _env(fp, peps, pepo, D=2, w=4, chi=12, prec="f64", seed=5)
+    fp.fpeps_absorb_row(env.h, 0, 1)
+    fp.fpeps_absorb_row(env.h, 1, 1)
+    # one Theta application at site 1 with a random left environment
+    g = np.random.default_rng(0)
+    A, W = peps[1][1], pepo[1][1]
+    t, tp = T[1].shape[0], T[1].shape[2]
+    dL, dR, dD = B.bdim(A, W, 0), B.bdim(A, W, 2), B.bdim(A, W, 3)
+    el = g.standard_normal((5, t, dL))
+    x = g.standard_normal((3, tp, dR))
+    y = env.apply_theta(1, el, x, dD)
+    yo = B.theta(el, T[1], A, W, np.moveaxis(x, 0, -1))            # [a, Dn, k]
+    assert np.allclose(np.moveaxis(y, 0, -1), yo, rtol=1e-11, atol=1e-13 * np.abs(yo).max())
+    fp.fpeps_compress_rsvd(env.h, fp.params(6, 2, 0, 1, 0))
+    for c in range(3):
+        sv = np.array(fp.fpeps_bond_spectrum(env.h, 0, c))
+        assert np.allclose(sv, res.zip_spectra[c], rtol=1e-9, atol=1e-12 * sv.max())
+    for c in range(3):
+        sv = np.array(fp.fpeps_bond_spectrum(env.h, 1, c))
+        assert np.allclose(sv, res.fit_spectra[c], rtol=1e-9, atol=1e-12 * sv.max())
+    # boundary shapes follow the oracle's
+    for c in range(4):
+        assert fp.fpeps_boundary_shape(env.h, c) == res.T[c].shape
+    env.close()
+
+
+def test_checkpoint_roundtrip_and_state_errors(fp):
+    peps = L.random_peps(4, 3, 2, 4, seed=6)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 3, 4, 2, seed=6))
+    env = _env(fp, peps, pepo, D=2, w=4, chi=10, prec="f64", seed=2)
+    prm = fp.params(5, 1, 0, 1, 0)
+    fp.fpeps_absorb_row(env.h, 0, 1)
+    with pytest.raises(fp.FpepsError) as ei:
+        fp.fpeps_absorb_row(env.h, 2, 1)          # out of order
+    assert ei.value.status == 2
+    fp.fpeps_absorb_row(env.h, 1, 1)
+    with pytest.raises(fp.FpepsError):
+        fp.fpeps_absorb_row(env.h, 2, 1)          # compress pending
+    fp.fpeps_compress_rsvd(env.h, prm)
+    blob = fp.fpeps_export_boundary(env.h)
+    fp.fpeps_absorb_row(env.h, 2, 1)
+    fp.fpeps_compress_rsvd(env.h, prm)
+    fp.fpeps_absorb_row(env.h, 3, 1)
+    v1 = fp.fpeps_sweep_value(env.h)
+    fp.fpeps_import_boundary(env.h, blob, 2, 1)
+    fp.fpeps_absorb_row(env.h, 2, 1)
+    fp.fpeps_compress_rsvd(env.h, prm)
+    fp.fpeps_absorb_row(env.h, 3, 1)
+    v2 = fp.fpeps_sweep_value(env.h)
+    assert v1[0] == v2[0] and abs(v1[1] - v2[1]) < 1e-12
+    with pytest.raises(fp.FpepsError) as ei:
+        fp.fpeps_compress_rsvd(env.h, prm)        # nothing staged
+    assert ei.value.status == 2
+    env.close()
+
+
+def test_product_state_closed_form_on_gpu(fp):
+    peps, vecs = L.product_peps(5, 4, 3, 4, seed=8)
+    ham = L.random_hamiltonian(5, 4, 4, 2, seed=8)
+    env = _env(fp, peps, L.fsm_pepo(ham), D=3, w=4, chi=20, prec="f64", seed=2)
+    val, sn, ln = env.expect(fp.params(4, 1, 0, 1, 0))
+    env.close()
+    assert abs(val - N.product_state_energy(vecs, ham)) < 1e-9 * max(1.0, abs(val))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 1e-3)])
+def test_c2_against_stored_oracle(fp, prec, tol):
+    """4x4, D=4, w=4, chi=64 truncated; oracle values written by tests/golden/make_golden.py."""
+    path = os.path.join(HERE, "golden", "c2_fsm_seed0.json")
+    gold = json.load(open(path))
+    peps = L.random_peps(4, 4, 4, 4, seed=gold["peps_seed"])
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=gold["ham_seed"]))
+    env = _env(fp, peps, pepo, D=4, w=4, chi=64, prec=prec, seed=gold["sketch_seed"])
+    val, sn, ln = env.expect(fp.params(10, 2, 0, 1, 0))
+    sd, ld = env.norm(fp.params(10, 2, 0, 1, 0))
+    env.close()
+    assert sn == gold["num_sign"] and sd == gold["den_sign"]
+    assert abs(ln - gold["num_log"]) < tol
+    assert abs(ld - gold["den_log"]) < tol
