@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Row-absorption benchmark: one boundary-MPS row absorbed and compressed back
+to chi by zip-up rSVD plus one CBE fit pass, on the 8x8, D=6, w=6
+(Hubbard-shaped FSM PEPO), chi=500 workload, central row r=4.
+
+One step = fpeps_import_boundary (device-resident seeded boundary of rows 0-3)
++ fpeps_absorb_row(4) + fpeps_compress_rsvd. The metric is algorithmic
+TFLOP/s of the contractions (the Fig. 2(a) applications; QR/SVD flops are not
+counted), the e2e number the same through host buffers (H2D of the boundary,
+D2H of the new boundary inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|f32|f64]
+  python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+Under torchrun (N > 1) every rank runs an independent replica (own seed); the
+timing is the max over ranks and the value counts the work of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "8x8 D=6 chi=500 row-absorb+rSVD s & TFLOP/s, mixed vs FP32; rel err vs FP64"
+WORKLOAD = "8x8 PEPS D=6 p=4, Hubbard-shaped FSM PEPO w=6 (K=4), chi=500, central row 4 absorbed into a seeded " \
+           "boundary (bonds 216/500), zip-up rSVD (oversample 10, q=2) + 1 CBE fit pass"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "f32", "f64"])
+    ap.add_argument("--workload", default="C4", choices=["C3", "C4"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def cpu_sample(seconds: float, workload):
+    """The FP64 oracle as it stands on a bounded sample of the same workload: Theta_c
+    applications at the central site c = Ly/2 - 1 (zip-up) on a few sketch columns.
+    Returns (TFLOP/s, description, cores)."""
+    import numpy as np
+
+    from oracle import boundary as OB
+    w = workload
+    c = w.Ly // 2 - 1
+    A, W = w.peps[w.row][c], w.pepo[w.row][c]
+    T = w.boundary[c]
+    t, tp = T.shape[0], T.shape[2]
+    dL, dR, dD = OB.bdim(A, W, 0), OB.bdim(A, W, 2), OB.bdim(A, W, 3)
+    a = min(w.chi, t * dL)
+    g = np.random.default_rng(0)
+    EL = g.standard_normal((a, t, dL))
+    nch = sum(1 for idx in np.ndindex(*W.shape[:4]) if np.any(W[idx] != 0))
+    n_ld = len({(i[0], i[3]) for i in np.ndindex(*W.shape[:4]) if np.any(W[i] != 0)})
+    D6p = A.shape[0] ** 2 * A.shape[1] ** 2 * A.shape[2] * A.shape[3] * A.shape[4]
+
+    def flops(k):   # same algorithmic count as the GPU path (structural PEPO zeros not counted)
+        sand = 2.0 * t * k * A.shape[4] * (nch * (A.shape[1] * A.shape[2]) ** 2 * A.shape[0] * A.shape[3]
+                                           + n_ld * (A.shape[0] * A.shape[3]) ** 2 * A.shape[1] * A.shape[2])
+        return 2.0 * t * T.shape[1] * tp * dR * k + sand + 2.0 * a * t * dL * dD * k
+
+    k = 1
+    done, tot_f, tot_t = 0, 0.0, 0.0
+    t_end = time.time() + seconds
+    while time.time() < t_end or done == 0:
+        X = g.standard_normal((tp, dR, k))
+        t0 = time.time()
+        OB.theta(EL, T, A, W, X)
+        tot_t += time.time() - t0
+        tot_f += flops(k)
+        done += k
+        k = min(4, k * 2)
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        cores = max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        cores = os.cpu_count()
+    desc = f"{done} Theta_c applications (column vectors) at site {c} of row {w.row}: chi={a}, t={t}, t'={tp}, " \
+           f"bundles {dL}/{dR}/{dD}, numpy FP64"
+    return tot_f / tot_t / 1e12, desc, cores
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    from paper_2511_01039_gb300 import workloads as WL
+
+    cfg = dict(getattr(WL, args.workload))
+    wl = WL.hubbard_row(seed=rank, **cfg)
+
+    if args.impl == "reference":
+        if rank != 0:
+            if dist:
+                dist.barrier()
+                dist.destroy_process_group()
+            return
+        per = []
+        for _ in range(args.warmup + args.steps):
+            v, desc, cores = cpu_sample(max(2.0, args.cpu_seconds / 3), wl)
+            per.append(v)
+        v = statistics.median(per[args.warmup:] or per)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+                "config": {"workload": WORKLOAD, "oracle": "numpy FP64, host cores"},
+                "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    from paper_2511_01039_gb300 import fpeps as fp
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    elem = 8 if args.prec == "f64" else 4
+    env = fp.Env(wl.peps, wl.pepo, D=wl.D, p=wl.p, w=wl.w, chi=wl.chi, prec=args.prec, seed=1 + rank)
+    prm = fp.params(oversample=10, power_iters=2, chi_tilde=0, n_fit=1, exact_svd=0)
+    blob = WL.boundary_blob(wl.boundary, wl.row, 1, elem)
+    dblob = torch.frombuffer(bytearray(blob), dtype=torch.uint8).to(dev)   # resident checkpoint
+    stream = env.stream
+
+    def step(src_ptr, nbytes):
+        lib = fp.lib()
+        fp._check(env.h, lib.fpeps_import_boundary(env.h, src_ptr, nbytes, wl.row, 1))
+        fp.fpeps_absorb_row(env.h, wl.row, 1)
+        return fp.fpeps_compress_rsvd(env.h, prm)
+
+    for _ in range(args.warmup):
+        step(dblob.data_ptr(), len(blob))
+    torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    fp.fpeps_profile(True)
+    n0 = fp.fpeps_launch_count()
+    flops = 0.0
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step(dblob.data_ptr(), len(blob))
+            flops += st.alg_flops
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = fp.fpeps_launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    prof = {fp.PROF_KINDS[k]: fp.fpeps_profile_read(k) for k in fp.PROF_KINDS}
+    fp.fpeps_profile(False)
+    tot_flops = flops
+    if dist:
+        t = torch.tensor([ms, flops], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, tot_flops = mx[0].item(), sm[1].item()
+    value = tot_flops / (ms * 1e-3) / 1e12
+
+    # ---------------- end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ef = 0.0
+        d2h = 0
+        for _ in range(args.steps):
+            st = step(fp.C.cast(fp.C.c_char_p(blob), fp.C.c_void_p).value, len(blob))
+            out = fp.fpeps_export_boundary(env.h)
+            d2h = len(out)
+            ef += st.alg_flops
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el, ef], dtype=torch.float64, device=dev)
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            sm = t.clone()
+            dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+            el, ef = mx[0].item(), sm[1].item()
+        e2e = {"value": ef / el / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": len(blob), "d2h_bytes_per_step": d2h,
+               "seconds_per_step": el / args.steps}
+
+    # ---------------- roofline of the dominant kernel class
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "of measured" if peaks else "of fallback"
+    d = prof[dom]
+    if dom in ("gemm_tc_tf32x3",):
+        # TF32 dense peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1/2.25)
+        peak = bf16 * 1.1 / 2.25
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "note": f"algorithmic flops; 3xTF32 issues 3 MMAs per product so frac <= 1/3 ({src} BF16 x 1.1/2.25)"}
+    elif dom in ("gemm_simt", "sandwich"):
+        peak = 80.0
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom,
+                "note": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz ~ 80 TFLOP/s"}
+    else:
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom}
+    per_kind = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                    "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None} for k, v in prof.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world if dist else args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "seconds_per_row": ms / args.steps / 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 data, 3xTF32 tensor-core products" if args.prec == "tf32x3" else args.prec,
+            "data": "synthetic (seeded PEPS, Hubbard-shaped PEPO, random boundary)",
+            "config": {"workload": WORKLOAD, "precision": args.prec, "l2": "inputs and intermediates >> 129 MB L2",
+                       "parallelism": f"replicas x{world}" if dist else "1 GPU",
+                       "alg_flops_per_step": flops / args.steps},
+            "roofline": roof, "kernels": per_kind, "gpu_launches": launches, "clocks": clk.summary()}
+    if e2e:
+        line["e2e"] = e2e
+    env.close()
+    if rank == 0 and not args.no_cpu:
+        v, desc, cores = cpu_sample(args.cpu_seconds, wl)
+        line["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

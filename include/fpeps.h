@@ -152,7 +152,10 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
 
 /* Load a boundary (same layout as fpeps_export_boundary, from any source with
  * the right shapes) and make `next_row` the next row to absorb in `layer`.
- * The tensors are copied host -> device on the env stream. */
+ * `host_buf` may point to host memory (copied host -> device, the call
+ * synchronises) or to device memory (copied device -> device on the env
+ * stream, only the header is read back). The buffer must stay valid until the
+ * copies have executed. */
 fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t bytes, int32_t next_row,
                                    int32_t layer);
 
@@ -180,6 +183,35 @@ fpeps_status fpeps_bond_spectrum(const fpeps_env* env, int32_t which, int32_t c,
  * Element type = compute precision. Synchronises the stream. */
 fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void* el_host, int32_t k,
                                const void* x_host, void* y_host);
+
+/* One contraction GEMM of the path on caller device buffers (diagnostic):
+ * C[M][N] (row-major) = sum_k A[m][k] B[n][k]; A [M][lda], B [N][ldb] fp32.
+ * mode FPEPS_F32: CUDA-core FP32; FPEPS_TF32X3: tensor-core 3xTF32 (needs
+ * M, N >= 128, K >= 32, lda and ldb multiples of 4, 16-byte aligned A and B,
+ * else FPEPS_ERR_UNSUPPORTED). Synchronises `cuda_stream` for TF32X3. */
+fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                            const float* B, int64_t ldb, float* C, void* cuda_stream);
+
+/* Small dense SVD of the path (diagnostic), FP64, one-sided Jacobi:
+ * M (k x k, column-major, device, not modified) = U diag(sigma) V^T with sigma
+ * descending and U, V column-major k x k (device). Columns whose singular value
+ * is below 1e-15 of the Frobenius norm get a zero U column. 1 <= k <= 1024.
+ * Allocates its scratch (2 k^2 doubles) with cudaMallocAsync on `cuda_stream`
+ * and synchronises it. */
+fpeps_status fpeps_svd_f64(const double* M, int32_t k, double* U, double* sigma, double* V, void* cuda_stream);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t fpeps_launch_count(void);
+
+/* Per-kernel-class timing with CUDA events recorded on the launching stream.
+ * fpeps_profile(1) clears the records and starts recording, fpeps_profile(0)
+ * clears and stops. fpeps_profile_read(kind) returns, for the recorded
+ * launches of one class, their count, summed device time (ms), summed
+ * algorithmic flops and summed algorithmic bytes; it synchronises on the
+ * recorded events. kind: 0 tensor-core GEMM, 1 CUDA-core GEMM, 2 sandwich,
+ * 3 Gram, 4 small factorisations (Cholesky, inverse, Jacobi). */
+fpeps_status fpeps_profile(int32_t enable);
+fpeps_status fpeps_profile_read(int32_t kind, int64_t* launches, double* ms, double* flops, double* bytes);
 
 /* Library version string. */
 const char* fpeps_version(void);

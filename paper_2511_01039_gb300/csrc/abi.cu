@@ -1,6 +1,8 @@
 // C ABI of libfpeps: environment lifecycle, the row state machine and
 // checkpoints. Every entry point converts internal errors to fpeps_status.
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -34,6 +36,41 @@ void Allocator::put(void* p) {
     return;
   }
   cudaFreeAsync(p, stream);
+}
+
+// ------------------------------------------------------------------ accounting
+namespace {
+std::atomic<long long> g_launches{0};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct ProfRec {
+  cudaEvent_t e0, e1;
+  double flops, bytes;
+};
+std::vector<ProfRec> g_prof[PROF_KINDS];
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfToken prof_begin(int kind, cudaStream_t s, double flops, double bytes) {
+  ProfToken t;
+  if (!g_prof_on) return t;
+  t.kind = kind;
+  t.flops = flops;
+  t.bytes = bytes;
+  FP_CUDA(cudaEventCreate(&t.e0));
+  FP_CUDA(cudaEventRecord(t.e0, s));
+  return t;
+}
+
+void prof_end(ProfToken& t, cudaStream_t s) {
+  if (t.kind < 0) return;
+  cudaEvent_t e1;
+  FP_CUDA(cudaEventCreate(&e1));
+  FP_CUDA(cudaEventRecord(e1, s));
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof[t.kind].push_back(ProfRec{t.e0, e1, t.flops, t.bytes});
+  t.kind = -1;
 }
 
 namespace {
@@ -359,7 +396,18 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
     const int Ly = env->cfg.Ly;
     size_t head = sizeof(int64_t) * (5 + (Ly + 1) + Ly) + sizeof(double);
     if (bytes < head) throw Error{FPEPS_ERR_ARG, "buffer too small"};
-    const char* p = (const char*)host_buf;
+    // the checkpoint may live in host or in device memory
+    cudaPointerAttributes pa;
+    bool on_dev = cudaPointerGetAttributes(&pa, host_buf) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    std::vector<char> hcopy;
+    const char* src = (const char*)host_buf;
+    if (on_dev) {
+      hcopy.resize(head);
+      FP_CUDA(cudaMemcpyAsync(hcopy.data(), host_buf, head, cudaMemcpyDeviceToHost, env->stream));
+      FP_CUDA(cudaStreamSynchronize(env->stream));
+    }
+    const char* p = on_dev ? hcopy.data() : src;
     const int64_t* h = (const int64_t*)p;
     if (h[0] != fpeps::kMagic || h[1] != Ly || h[4] != env->elem) throw Error{FPEPS_ERR_ARG, "bad checkpoint header"};
     if (next_row < 1 || next_row >= env->cfg.Lx) throw Error{FPEPS_ERR_ARG, "next_row out of range"};
@@ -381,17 +429,18 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
     for (int c = 0; c < Ly; ++c) {
       size_t nb = (size_t)tb[c] * ph[c] * tb[c + 1] * env->elem;
       env->T[c] = env->al.get(nb);
-      FP_CUDA(cudaMemcpyAsync(env->T[c], p + off, nb, cudaMemcpyHostToDevice, env->stream));
+      FP_CUDA(cudaMemcpyAsync(env->T[c], src + off, nb, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              env->stream));
       off += nb;
     }
     std::memcpy(&env->log_scale, p + head - sizeof(double), sizeof(double));
+    if (!on_dev) FP_CUDA(cudaStreamSynchronize(env->stream));
     env->tb = tb;
     env->tphys = ph;
     env->layer = layer;
     env->next_row = next_row;
     env->state = fpeps::RowState::Ready;
     env->have_value = false;
-    FP_CUDA(cudaStreamSynchronize(env->stream));
   });
 }
 
@@ -451,6 +500,85 @@ fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void*
       throw Error{FPEPS_ERR_ARG, "bad argument"};
     env->engine->apply_theta_host(env, c, a, el_host, k, x_host, y_host);
   });
+}
+
+fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                            const float* B, int64_t ldb, float* C, void* cuda_stream) {
+  return fpeps::guard(nullptr, [&] {
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || lda < K || ldb < K) throw Error{FPEPS_ERR_ARG, "bad GEMM"};
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const fpeps::OutMap om = fpeps::out_rowmajor(M, N, N);
+    if (mode == FPEPS_F32) {
+      fpeps::gemm_simt<float>(s, M, N, K, 1.0f, A, lda, 1, B, ldb, 1, 0.0f, C, om);
+      return;
+    }
+    if (mode != FPEPS_TF32X3) throw Error{FPEPS_ERR_UNSUPPORTED, "mode"};
+    if (!fpeps::gemm_tc_supported(M, N, K, lda, ldb) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16))
+      throw Error{FPEPS_ERR_UNSUPPORTED, "shape not supported by the tensor-core kernel"};
+    int* err = nullptr;
+    FP_CUDA(cudaMallocAsync((void**)&err, 256, s));
+    FP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    fpeps::gemm_tc(s, mode, M, N, K, A, lda, B, ldb, C, om, err, 256);
+    int h = 0;
+    FP_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+    cudaFreeAsync(err, s);
+    if (h) throw Error{FPEPS_ERR_TIMEOUT, "tensor-core GEMM timed out"};
+  });
+}
+
+fpeps_status fpeps_svd_f64(const double* M, int32_t k, double* U, double* sigma, double* V, void* cuda_stream) {
+  return fpeps::guard(nullptr, [&] {
+    if (!M || !U || !sigma || !V || k < 1 || k > 1024) throw Error{FPEPS_ERR_ARG, "bad SVD arguments"};
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t kk = (size_t)k * k;
+    char* scr = nullptr;
+    const size_t bytes = 2 * kk * sizeof(double) + ((size_t)k * sizeof(int) + 255) / 256 * 256 + 256;
+    FP_CUDA(cudaMallocAsync((void**)&scr, bytes, s));
+    double* Mw = (double*)scr;
+    double* Vw = Mw + kk;
+    int* order = (int*)(Vw + kk);
+    void* ws = scr + bytes - 256;
+    int* info = (int*)ws + 32;
+    FP_CUDA(cudaMemcpyAsync(Mw, M, kk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    fpeps::svd_jacobi_f64(s, Mw, k, U, sigma, Vw, order, info, ws);
+    fpeps::gather_cols_f64(s, Vw, order, k, V);
+    FP_CUDA(cudaFreeAsync(scr, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int64_t fpeps_launch_count(void) { return fpeps::g_launches.load(); }
+
+fpeps_status fpeps_profile(int32_t enable) {
+  std::lock_guard<std::mutex> lk(fpeps::g_prof_mu);
+  for (auto& v : fpeps::g_prof)
+    for (auto& r : v) {
+      cudaEventDestroy(r.e0);
+      cudaEventDestroy(r.e1);
+    }
+  for (auto& v : fpeps::g_prof) v.clear();
+  fpeps::g_prof_on = enable != 0;
+  return FPEPS_OK;
+}
+
+fpeps_status fpeps_profile_read(int32_t kind, int64_t* launches, double* ms, double* flops, double* bytes) {
+  if (kind < 0 || kind >= fpeps::PROF_KINDS || !launches || !ms || !flops || !bytes) return FPEPS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(fpeps::g_prof_mu);
+  double t = 0, f = 0, b = 0;
+  for (auto& r : fpeps::g_prof[kind]) {
+    if (cudaEventSynchronize(r.e1) != cudaSuccess) return FPEPS_ERR_CUDA;
+    float x = 0;
+    if (cudaEventElapsedTime(&x, r.e0, r.e1) != cudaSuccess) return FPEPS_ERR_CUDA;
+    t += x;
+    f += r.flops;
+    b += r.bytes;
+  }
+  *launches = (int64_t)fpeps::g_prof[kind].size();
+  *ms = t;
+  *flops = f;
+  *bytes = b;
+  return FPEPS_OK;
 }
 
 const char* fpeps_version(void) { return "fpeps-gb300 0.1 (sm_103a)"; }

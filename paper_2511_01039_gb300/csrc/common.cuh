@@ -29,7 +29,25 @@ struct Error {
     if (!(cond)) throw ::fpeps::Error{code, std::string(text)};      \
   } while (0)
 
-#define FP_LAUNCH() FP_CUDA(cudaGetLastError())
+// ---------------------------------------------------------------- launch accounting
+// Every kernel launch of the library goes through FP_LAUNCH (count), and the
+// hot kernel classes can be bracketed with CUDA events (prof_begin/prof_end)
+// when profiling is enabled, so callers can time them on their own stream.
+enum ProfKind { PROF_GEMM_TC = 0, PROF_GEMM_SIMT = 1, PROF_SANDWICH = 2, PROF_GRAM = 3, PROF_FACTOR = 4, PROF_KINDS = 5 };
+void count_launch();
+struct ProfToken {
+  int kind = -1;
+  cudaEvent_t e0 = nullptr;
+  double flops = 0, bytes = 0;
+};
+ProfToken prof_begin(int kind, cudaStream_t s, double flops, double bytes);
+void prof_end(ProfToken& t, cudaStream_t s);
+
+#define FP_LAUNCH()                  \
+  do {                               \
+    ::fpeps::count_launch();         \
+    FP_CUDA(cudaGetLastError());     \
+  } while (0)
 
 // ---------------------------------------------------------------- memory
 // Device memory owned through the env allocator. Arena buffers are released in
@@ -98,6 +116,12 @@ void sandwich_apply(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk,
                     int64_t i_t, int64_t i_k, int64_t i_X, int64_t i_Y, T* out, int64_t o_t, int64_t o_k,
                     int64_t o_V, int64_t o_Z);
 
+// 3xTF32 tensor-core version (mma.sync), float data; needs D^2 <= 40, D^2 p <= 144.
+bool sandwich_mma_fits(const SandOrient& o);
+void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const float* in, int64_t i_t,
+                       int64_t i_k, int64_t i_X, int64_t i_Y, float* out, int64_t o_t, int64_t o_k, int64_t o_V,
+                       int64_t o_Z);
+
 // Builds the role-permuted ket and the channel products A.W_ch for one orientation.
 // roles[4] = leg index (0..3 = l,u,r,d) of (x, y, v, z).
 template <class T>
@@ -121,11 +145,17 @@ template <class T>
 void gram_f64(cudaStream_t s, const T* Y, int64_t m, int64_t k, int64_t ld, double* G);
 
 // returns device status word pointer semantics: info[0] != 0 on failure
-void cholesky_upper_f64(cudaStream_t s, double* G, int k, int* info);
+// ws: >= 8 bytes of device scratch
+void cholesky_upper_f64(cudaStream_t s, double* G, int k, int* info, double* ws);
 void tri_inverse_upper_f64(cudaStream_t s, const double* R, int k, double* Rinv);
 void sym_eig_jacobi_f64(cudaStream_t s, double* G, int k, double* evec, double* eval, int* info);
+// One-sided Jacobi SVD of the k x k col-major Mat (destroyed): Mat = U diag(sigma) V^T,
+// sigma descending; U columns sorted, V columns in original order with order[rank] =
+// original column. ws_dev: >= 64 bytes of device scratch.
 void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma, double* V, int* order,
-                    int* info);
+                    int* info, void* ws_dev);
+
+void gather_cols_f64(cudaStream_t s, const double* V, const int* order, int k, double* out);
 
 template <class T>
 void convert_f64(cudaStream_t s, const double* in, T* out, int64_t n);

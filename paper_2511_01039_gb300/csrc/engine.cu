@@ -17,6 +17,8 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <chrono>
+#include <cstdio>
 #include <functional>
 
 #include "env.cuh"
@@ -125,9 +127,32 @@ struct Engine : EngineBase {
   size_t scr_n[2] = {0, 0};
   void* tc_scr = nullptr;
   size_t tc_n = 0;
+  bool tc_used = false;
+
+  // optional per-phase wall times (FPEPS_TRACE=1): synchronises around each phase
+  bool trace = false;
+  double ph[6] = {0, 0, 0, 0, 0, 0};   // apply, qr, svd, sketch, small, total
+  struct Phase {
+    Engine* e;
+    int i;
+    std::chrono::steady_clock::time_point t0;
+    Phase(Engine* en, int idx) : e(en), i(idx) {
+      if (e->trace) {
+        cudaStreamSynchronize(e->s);
+        t0 = std::chrono::steady_clock::now();
+      }
+    }
+    ~Phase() {
+      if (e->trace) {
+        cudaStreamSynchronize(e->s);
+        e->ph[i] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      }
+    }
+  };
 
   explicit Engine(fpeps_env* e) : env(e), s(e->stream), mode(e->cfg.prec) {
     if (const char* b = getenv("FPEPS_CHUNK_ELEMS")) budget_elems = (size_t)atoll(b);
+    if (const char* t = getenv("FPEPS_TRACE")) trace = atoi(t) != 0;
   }
   ~Engine() override {
     for (int i = 0; i < 2; ++i)
@@ -148,15 +173,19 @@ struct Engine : EngineBase {
   // C = A B^T, A [M][lda], B [N][ldb], both k-contiguous
   void big_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C, OutMap om) {
     flops += 2.0 * (double)M * (double)N * (double)K;
-    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3)) {
-      FP_CHECK(gemm_tc_supported(M, N, K, lda, ldb), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: unsupported shape");
+    // tensor cores for every contraction with at least one full 128x128x32 tile and
+    // 16-byte aligned rows; smaller edge contractions stay on the CUDA cores (FP32)
+    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && gemm_tc_supported(M, N, K, lda, ldb) &&
+        ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0) {
       size_t need = gemm_tc_scratch_bytes(mode, M, N, K);
-      if (tc_n < need) {
+      if (!tc_scr || tc_n < need) {
         if (tc_scr) env->al.put(tc_scr);
-        tc_scr = env->al.get(need);
-        tc_n = need;
+        tc_scr = env->al.get(std::max<size_t>(need, 256));
+        tc_n = std::max<size_t>(need, 256);
+        FP_CUDA(cudaMemsetAsync(tc_scr, 0, sizeof(int), s));
       }
       gemm_tc(s, mode, M, N, K, (const float*)A, lda, (const float*)B, ldb, (float*)C, om, tc_scr, tc_n);
+      tc_used = true;
       return;
     }
     gemm_simt<T>(s, M, N, K, T(1), A, lda, 1, B, ldb, 1, T(0), C, om);
@@ -189,6 +218,17 @@ struct Engine : EngineBase {
     const T* Et = nullptr;
   };
 
+  // the sandwich step: tensor cores (3xTF32, mma.sync) in the split-precision
+  // modes when the site fits the tile, CUDA cores otherwise
+  void sandwich(const SandOrient& o, int64_t nt, int64_t nk, const T* in, int64_t i_t, int64_t i_k, int64_t i_X,
+                int64_t i_Y, T* out, int64_t o_t, int64_t o_k, int64_t o_V, int64_t o_Z) {
+    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && sandwich_mma_fits(o)) {
+      sandwich_apply_tc(s, o, nt, nk, (const float*)in, i_t, i_k, i_X, i_Y, (float*)out, o_t, o_k, o_V, o_Z);
+      return;
+    }
+    sandwich_apply<T>(s, o, nt, nk, in, i_t, i_k, i_X, i_Y, out, o_t, o_k, o_V, o_Z);
+  }
+
   double sand_flops(const SandOrient& o, int64_t blocks, int n_ld) const {
     double ket = 2.0 * o.nch * (double)o.nx * o.nx * o.ny * o.ny * o.nv * o.nz * o.p;
     double bra = 2.0 * n_ld * (double)o.nv * o.nv * o.nz * o.nz * o.nx * o.ny * o.p;
@@ -209,6 +249,7 @@ struct Engine : EngineBase {
 
   // Y[k][Dn][a] = Theta_c X,  X[k][R][t']
   void theta(const Site& st, const Env3& el, const T* X, T* Y, int64_t k) {
+    Phase ph_(this, 0);
     const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = el.a;
     const SandOrient& o = st.sd->o[FWD];
     const int64_t kc = chunk_k(k, t * std::max(U * R, L * Dn));
@@ -217,13 +258,19 @@ struct Engine : EngineBase {
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
       const int64_t kk = std::min(kc, k - k0);
       big_gemm(t * U, kk * R, tp, st.Tm, tp, X + k0 * R * tp, tp, G1, OutMap{U, kk * U * R, R, R, U * R, 1});
-      sandwich_apply<T>(s, o, t, kk, G1, kk * U * R, U * R, R, 1, G2, L, Dn * t * L, 1, t * L);
-      flops += sand_flops(o, t * kk, st.sd->n_ld);
+      {
+        const double sf = sand_flops(o, t * kk, st.sd->n_ld);
+        ProfToken pt = prof_begin(PROF_SANDWICH, s, sf, (double)sizeof(T) * t * kk * (double)(U * R + L * Dn));
+        sandwich(o, t, kk, G1, kk * U * R, U * R, R, 1, G2, L, Dn * t * L, 1, t * L);
+        prof_end(pt, s);
+        flops += sf;
+      }
       big_gemm(a, kk * Dn, t * L, el.E, t * L, G2, t * L, Y + k0 * Dn * a, OutMap{a, 0, 1, Dn, Dn * a, a});
     }
   }
   // Z[k][R][t'] = Theta_c^T Y,  Y[k][Dn][a]
   void theta_t(const Site& st, const Env3& el, const T* Y, T* Z, int64_t k) {
+    Phase ph_(this, 0);
     const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = el.a;
     const SandOrient& o = st.sd->o[BWD];
     const int64_t kc = chunk_k(k, t * std::max(U * R, L * Dn));
@@ -232,13 +279,19 @@ struct Engine : EngineBase {
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
       const int64_t kk = std::min(kc, k - k0);
       big_gemm(t * L, kk * Dn, a, el.Et, a, Y + k0 * Dn * a, a, H1, OutMap{L, kk * L * Dn, Dn, Dn, L * Dn, 1});
-      sandwich_apply<T>(s, o, t, kk, H1, kk * L * Dn, L * Dn, Dn, 1, H2, U, R * t * U, 1, t * U);
-      flops += sand_flops(o, t * kk, st.sd->n_ld);
+      {
+        const double sf = sand_flops(o, t * kk, st.sd->n_ld);
+        ProfToken pt = prof_begin(PROF_SANDWICH, s, sf, (double)sizeof(T) * t * kk * (double)(U * R + L * Dn));
+        sandwich(o, t, kk, H1, kk * L * Dn, L * Dn, Dn, 1, H2, U, R * t * U, 1, t * U);
+        prof_end(pt, s);
+        flops += sf;
+      }
       big_gemm(tp, kk * R, t * U, st.Tt, t * U, H2, t * U, Z + k0 * R * tp, OutMap{tp, 0, 1, R, R * tp, tp});
     }
   }
   // Z[k][L][t] = ThetaR_c X,  X[k][Dn][a_c]; er = environment to the right of site c
   void theta_r(const Site& st, const Env3& er, const T* X, T* Z, int64_t k) {
+    Phase ph_(this, 0);
     const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = er.a;
     const SandOrient& o = st.sd->o[RF];
     const int64_t kc = chunk_k(k, tp * std::max(R * Dn, L * U));
@@ -247,13 +300,19 @@ struct Engine : EngineBase {
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
       const int64_t kk = std::min(kc, k - k0);
       big_gemm(tp * R, kk * Dn, a, er.Et, a, X + k0 * Dn * a, a, W1, OutMap{R, kk * R * Dn, Dn, Dn, R * Dn, 1});
-      sandwich_apply<T>(s, o, tp, kk, W1, kk * R * Dn, R * Dn, Dn, 1, W2, U, L * tp * U, tp * U, 1);
-      flops += sand_flops(o, tp * kk, st.sd->n_ld);
+      {
+        const double sf = sand_flops(o, tp * kk, st.sd->n_ld);
+        ProfToken pt = prof_begin(PROF_SANDWICH, s, sf, (double)sizeof(T) * tp * kk * (double)(U * R + L * Dn));
+        sandwich(o, tp, kk, W1, kk * R * Dn, R * Dn, Dn, 1, W2, U, L * tp * U, tp * U, 1);
+        prof_end(pt, s);
+        flops += sf;
+      }
       big_gemm(t, kk * L, tp * U, st.Tp, tp * U, W2, tp * U, Z + k0 * L * t, OutMap{t, 0, 1, L, L * t, t});
     }
   }
   // X[k][Dn][a_c] = ThetaR_c^T Z,  Z[k][L][t]
   void theta_r_t(const Site& st, const Env3& er, const T* Z, T* X, int64_t k) {
+    Phase ph_(this, 0);
     const int64_t t = st.t, tp = st.tp, U = st.bU, R = st.bR, L = st.bL, Dn = st.bD, a = er.a;
     const SandOrient& o = st.sd->o[RB];
     const int64_t kc = chunk_k(k, tp * std::max(R * Dn, L * U));
@@ -262,8 +321,13 @@ struct Engine : EngineBase {
     for (int64_t k0 = 0; k0 < k; k0 += kc) {
       const int64_t kk = std::min(kc, k - k0);
       big_gemm(tp * U, kk * L, t, st.Tq, t, Z + k0 * L * t, t, W1, OutMap{U, kk * L * U, 1, L, L * U, U});
-      sandwich_apply<T>(s, o, tp, kk, W1, kk * L * U, L * U, U, 1, W2, R, Dn * tp * R, 1, tp * R);
-      flops += sand_flops(o, tp * kk, st.sd->n_ld);
+      {
+        const double sf = sand_flops(o, tp * kk, st.sd->n_ld);
+        ProfToken pt = prof_begin(PROF_SANDWICH, s, sf, (double)sizeof(T) * tp * kk * (double)(U * R + L * Dn));
+        sandwich(o, tp, kk, W1, kk * L * U, L * U, U, 1, W2, R, Dn * tp * R, 1, tp * R);
+        prof_end(pt, s);
+        flops += sf;
+      }
       big_gemm(a, kk * Dn, tp * R, er.E, tp * R, W2, tp * R, X + k0 * Dn * a, OutMap{a, 0, 1, Dn, Dn * a, a});
     }
   }
@@ -275,13 +339,22 @@ struct Engine : EngineBase {
     frob_norm_f64<T>(s, x, n, env->d_scal);
     FP_CUDA(cudaMemcpyAsync(env->h_scal, env->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     FP_CUDA(cudaStreamSynchronize(s));
+    check_tc();
     double v = env->h_scal[0];
     FP_CHECK(std::isfinite(v), FPEPS_ERR_NUMERIC, "non-finite norm");
     return v;
   }
+  // the tensor-core kernels record a bounded-wait timeout in their error word
+  void check_tc() {
+    if (!tc_used) return;
+    FP_CUDA(cudaMemcpyAsync(env->h_info + 1, tc_scr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaStreamSynchronize(s));
+    if (env->h_info[1]) throw Error{FPEPS_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait timed out"};
+  }
   int read_info() {
     FP_CUDA(cudaMemcpyAsync(env->h_info, env->d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
     FP_CUDA(cudaStreamSynchronize(s));
+    check_tc();
     return env->h_info[0];
   }
 
@@ -343,7 +416,7 @@ struct Engine : EngineBase {
   void one_pass(Arena& ar, const T* Y, int64_t m, int k, T* Q, double* R) {
     double* G = ar.get_n<double>((int64_t)k * k);
     gram_f64<T>(s, Y, m, k, m, G);
-    cholesky_upper_f64(s, G, k, env->d_info);
+    cholesky_upper_f64(s, G, k, env->d_info, ar.get_n<double>(8));
     T* Bt = ar.get_n<T>((int64_t)k * k);
     if (read_info() == 0) {
       double* Rinv = ar.get_n<double>((int64_t)k * k);
@@ -356,7 +429,7 @@ struct Engine : EngineBase {
     }
     // SVQB
     gram_f64<T>(s, Y, m, k, m, G);
-    double* work = ar.get_n<double>((int64_t)6 * k * k + 4 * k);
+    double* work = ar.get_n<double>((int64_t)6 * k * k + 4 * k + 64);
     double* Bt64 = ar.get_n<double>((int64_t)k * k);
     double* Rq = ar.get_n<double>((int64_t)k * k);
     svqb_factors(s, G, k, work, Bt64, Rq, env->d_info);
@@ -368,6 +441,7 @@ struct Engine : EngineBase {
   }
 
   void qr(const T* Y, int64_t m, int k, T* Q, double* R) {
+    Phase ph_(this, 1);
     Arena ar = arena();
     T* Q1 = ar.get_n<T>(m * k);
     double* R1 = R ? ar.get_n<double>((int64_t)k * k) : nullptr;
@@ -417,7 +491,10 @@ struct Engine : EngineBase {
     double* Vj = ar.get_n<double>((int64_t)k * k);
     double* sg = ar.get_n<double>(k);
     int* order = ar.get_n<int>(k);
-    svd_jacobi_f64(s, Ms, k, Uj, sg, Vj, order, env->d_info);
+    {
+      Phase ph_(this, 2);
+      svd_jacobi_f64(s, Ms, k, Uj, sg, Vj, order, env->d_info, ar.get(64));
+    }
     FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "Jacobi SVD did not converge");
     r.U = Uj;
     double* Vs = ar.get_n<double>((int64_t)k * k);
@@ -512,6 +589,8 @@ struct Engine : EngineBase {
     ensure_sandwich(e, e->layer, row);
     flops = 0.0;
     trunc_num = trunc_den = 0.0;
+    for (double& v : ph) v = 0.0;
+    const auto t_start = std::chrono::steady_clock::now();
     cudaEvent_t ev0, ev1;
     FP_CUDA(cudaEventCreate(&ev0));
     FP_CUDA(cudaEventCreate(&ev1));
@@ -586,8 +665,10 @@ struct Engine : EngineBase {
       T* one = ar.get_n<T>(1);
       fill<T>(s, one, 1, T(1));
       const int64_t rows = (int64_t)EL[c].a * st.bD;
+      T* yv = ar.get_n<T>(rows);
+      theta(st, EL[c], one, yv, 1);                                  // [1][Dn][a]
       Nlast = rowmem.get_n<T>(rows);
-      theta(st, EL[c], one, Nlast, 1);
+      permute3<T>(s, yv, Nlast, 1, st.bD, EL[c].a, 0, 2, 1);        // -> [a][Dn][1]
       double nrm = host_norm(Nlast, rows);
       FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "zip-up last tensor vanished");
       scale_by_inv<T>(s, Nlast, rows, e->d_scal);
@@ -629,6 +710,11 @@ struct Engine : EngineBase {
     FP_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
+    if (trace) {
+      ph[5] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      fprintf(stderr, "[fpeps] row %d: total %.3f s  apply %.3f  qr %.3f  svd %.3f  (alg %.3e flop)\n", row, ph[5],
+              ph[0], ph[1], ph[2], flops);
+    }
     if (out) {
       out->seconds = ms * 1e-3;
       out->alg_flops = flops;
@@ -745,7 +831,10 @@ struct Engine : EngineBase {
       double* Vj = ar.get_n<double>((int64_t)j * j);
       double* sg = ar.get_n<double>(j);
       int* order = ar.get_n<int>(j);
-      svd_jacobi_f64(s, Rm, j, Uj, sg, Vj, order, e->d_info);
+      {
+        Phase ph_(this, 2);
+        svd_jacobi_f64(s, Rm, j, Uj, sg, Vj, order, e->d_info, ar.get(64));
+      }
       FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "Jacobi SVD did not converge (fit)");
       double* Vs = ar.get_n<double>((int64_t)j * j);
       gather_cols_f64(s, Vj, order, j, Vs);

@@ -84,8 +84,11 @@ void gemm_simt(cudaStream_t s, int64_t M, int64_t N, int64_t K, T alpha, const T
   FP_CHECK(om.mdiv > 0 && om.ndiv > 0, FPEPS_ERR_ARG, "gemm: bad output map");
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   FP_CHECK(grid.y <= 65535u, FPEPS_ERR_UNSUPPORTED, "gemm: M too large for grid");
+  ProfToken pt = prof_begin(PROF_GEMM_SIMT, s, 2.0 * M * N * K,
+                            (double)sizeof(T) * ((double)M * K + (double)N * K + (double)M * N));
   k_gemm<T><<<grid, 256, 0, s>>>(M, N, K, alpha, A, a_m, a_k, B, b_n, b_k, beta, C, om);
   FP_LAUNCH();
+  prof_end(pt, s);
 }
 
 template void gemm_simt<float>(cudaStream_t, int64_t, int64_t, int64_t, float, const float*, int64_t, int64_t,

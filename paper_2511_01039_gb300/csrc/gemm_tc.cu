@@ -1,13 +1,335 @@
-// Tensor-core split-precision GEMM (tcgen05 / TMEM / TMA) -- see below.
+// Split-precision tensor-core GEMM for sm_103a: tcgen05.mma with a TMEM
+// accumulator, operands staged in shared memory by TMA (cp.async.bulk.tensor).
+//
+//   C(m,n) = sum_k A[m][k] B[n][k]      A [M][lda], B [N][ldb] fp32, k contiguous
+//
+// This carries the two chi^2-class contractions of every Fig. 2(a) application
+// (boundary x vectors, environment x vectors). FP32 inputs are split on chip
+// into x = hi + lo and the product is a_hi b_hi + a_hi b_lo + a_lo b_hi with
+// FP32 accumulation in TMEM:
+//   mode 2 (3xTF32): hi = x rounded to TF32 (10-bit mantissa), lo = x - hi,
+//                    kind::tf32 MMAs on the 32-bit tiles.
+// One CTA computes a BM x BN tile. Warp roles: warp 0 issues TMA loads, warp 1
+// allocates TMEM and issues MMAs (one elected thread), warps 2-7 split each
+// landed stage into hi/lo tiles (in place + a second buffer, the swizzled
+// layout is preserved element by element), warps 4-7 then drain TMEM and store
+// C through the caller's output map. Every wait on an mbarrier is bounded: a
+// timeout sets an error word, the CTA stops issuing work, waits (bounded) for
+// what it has in flight, frees its TMEM and exits.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fpeps {
+namespace {
 
-bool gemm_tc_supported(int64_t, int64_t, int64_t, int64_t, int64_t) { return false; }
-size_t gemm_tc_scratch_bytes(int, int64_t, int64_t, int64_t) { return 0; }
-void gemm_tc(cudaStream_t, int, int64_t, int64_t, int64_t, const float*, int64_t, const float*, int64_t, float*, OutMap,
-             void*, size_t) {
-  throw Error{FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM not available"};
+constexpr int BM = 128, BN = 128, BK = 32;   // BK fp32 = 128 bytes = one 128B swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_A = BM * BK * 4, TILE_B = BN * BK * 4;       // bytes
+constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);               // hi + lo of A and B
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int NTHREADS = 256;
+constexpr int CONV_WARP0 = 2, N_CONV_WARPS = 6;
+constexpr unsigned long long WAIT_LIMIT = 2000000000ull;   // clock64 cycles (~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: returns false on timeout (and raises the CTA abort flag)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const unsigned long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_LIMIT) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
+  uint64_t a = (smem_u32(p) & 0x3FFFFu) >> 4;
+  return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_round(uint32_t bits) { return (bits + 0x1000u) & 0xFFFFE000u; }
+
+struct TcArgs {
+  int64_t M, N, K;
+  OutMap om;
+  float* C;
+  int* err;
+  int m_fast;   // rasterisation: 1 => consecutive blocks walk m
+  int64_t mt, nt;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tf32x3(const __grid_constant__ CUtensorMap mapA,
+                                                             const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* conv = full + STAGES;
+  uint64_t* empty = conv + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  // once any CTA has timed out, later CTAs do nothing (before touching TMEM or TMA)
+  if (*(volatile int*)g.err) return;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t bid = blockIdx.x;
+  const int64_t mt = g.m_fast ? bid % g.mt : bid / g.nt;
+  const int64_t ntile = g.m_fast ? bid / g.mt : bid % g.nt;
+  const int64_t m0 = mt * BM, n0 = ntile * BN;
+  const int nk = (int)((g.K + BK - 1) / BK);
+
+  auto A_hi = [&](int s) { return smem + s * STAGE_BYTES; };
+  auto B_hi = [&](int s) { return smem + s * STAGE_BYTES + TILE_A; };
+  auto A_lo = [&](int s) { return smem + s * STAGE_BYTES + TILE_A + TILE_B; };
+  auto B_lo = [&](int s) { return smem + s * STAGE_BYTES + 2 * TILE_A + TILE_B; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], N_CONV_WARPS);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;   // stages loaded by the producer (warp 0, lane 0)
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag)) break;
+        mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
+        tma_load_2d(A_hi(s), &mapA, &full[s], it * BK, (int)m0);
+        tma_load_2d(B_hi(s), &mapB, &full[s], it * BK, (int)n0);
+        ++issued;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // instruction descriptor: D f32, A/B tf32, both K-major, N>>3 at bit 17, M>>4 at bit 24
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      bool ok = true;
+      for (int it = 0; it < nk && ok; ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&conv[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ah = sdesc(A_hi(s)), bh = sdesc(B_hi(s)), al = sdesc(A_lo(s)), bl = sdesc(B_lo(s));
+#pragma unroll
+        for (int kk = 0; kk < BK / 8; ++kk) {   // 8 tf32 = 32 bytes per MMA
+          const uint64_t o = (uint64_t)(kk * 32) >> 4;
+          mma_tf32(tmem, al + o, bh + o, idesc, (it | kk) ? 1u : 0u);
+          mma_tf32(tmem, ah + o, bl + o, idesc, 1u);
+          mma_tf32(tmem, ah + o, bh + o, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(done);
+    }
+  } else {
+    // converter warps 2..7: x -> hi (in place), lo = x - hi
+    const int cw = warp - CONV_WARP0;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES;
+      if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) break;
+      uint4* ah = (uint4*)A_hi(s);
+      uint4* bh = (uint4*)B_hi(s);
+      uint4* alo = (uint4*)A_lo(s);
+      uint4* blo = (uint4*)B_lo(s);
+      for (int e = cw * 32 + lane; e < (TILE_A + TILE_B) / 16; e += N_CONV_WARPS * 32) {
+        uint4* src = e < TILE_A / 16 ? ah + e : bh + (e - TILE_A / 16);
+        uint4* dlo = e < TILE_A / 16 ? alo + e : blo + (e - TILE_A / 16);
+        uint4 v = *src;
+        uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+        uint4 l = make_uint4(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x)),
+                             __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y)),
+                             __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z)),
+                             __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w)));
+        *src = h;
+        *dlo = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+  }
+
+  // epilogue: warps 4..7 drain TMEM lanes 32*(warp%4) ..
+  if (warp >= 4) {
+    const bool ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int q = warp % 4;
+      const int64_t m = m0 + q * 32 + lane;
+      const bool mrow = m < g.M;
+      const int64_t mo = mrow ? (m / g.om.mdiv) * g.om.c0 + (m % g.om.mdiv) * g.om.c1 : 0;
+#pragma unroll 1
+      for (int cb = 0; cb < BN; cb += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (mrow) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t n = n0 + cb + j;
+            if (n < g.N) g.C[mo + (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) * g.om.c3] = __uint_as_float(r[j]);
+          }
+        }
+      }
+    }
+  }
+
+  // teardown: on abort, let the producer drain the loads it issued (bounded)
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it) {
+      const int s = it % STAGES;
+      const unsigned long long t0 = clock64();
+      while (!mbar_try_wait(&full[s], (it / STAGES) & 1) && clock64() - t0 < WAIT_LIMIT) {
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(g.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  });
+  FP_CHECK(fn != nullptr, FPEPS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+CUtensorMap make_map(const float* base, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  FP_CHECK(r == CUDA_SUCCESS, FPEPS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+}  // namespace
+
+bool gemm_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb) {
+  // TMA: 16-byte aligned row strides; tiles must have at least one full box
+  return M >= BM && N >= BN && K >= BK && (lda % 4) == 0 && (ldb % 4) == 0 && lda >= K && ldb >= K &&
+         M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31);
+}
+
+size_t gemm_tc_scratch_bytes(int, int64_t, int64_t, int64_t) { return 16; }
+
+void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+             int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes) {
+  FP_CHECK(mode == FPEPS_TF32X3, FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: only 3xTF32 is built");
+  FP_CHECK(scratch && scratch_bytes >= sizeof(int), FPEPS_ERR_ARG, "tensor-core GEMM: scratch");
+  FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
+  static bool attr = false;
+  if (!attr) {
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  CUtensorMap ma = make_map(A, M, K, lda, BM);
+  CUtensorMap mb = make_map(B, N, K, ldb, BN);
+  TcArgs g;
+  g.M = M; g.N = N; g.K = K; g.om = om; g.C = C; g.err = (int*)scratch;
+  g.mt = (M + BM - 1) / BM;
+  g.nt = (N + BN - 1) / BN;
+  g.m_fast = g.mt <= g.nt ? 1 : 0;
+  const int64_t blocks = g.mt * g.nt;
+  FP_CHECK(blocks < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: grid too large");
+  ProfToken pt = prof_begin(PROF_GEMM_TC, s, 2.0 * M * N * K, 4.0 * ((double)M * K + (double)N * K + (double)M * N));
+  k_gemm_tf32x3<<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(ma, mb, g);
+  FP_LAUNCH();
+  prof_end(pt, s);
 }
 
 }  // namespace fpeps

@@ -12,6 +12,8 @@
 // each rotation makes two columns orthogonal (Demmel and Veselic 1992).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fpeps {
@@ -89,6 +91,71 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Y, int64_t m
   }
 }
 
+// FP64-class Gram of FP32 data on the FP32 pipes. Each product a*b is split
+// exactly into p + e (p = fl(a*b), e = fma(a, b, -p)); p is accumulated with
+// an error-free two-sum into (hi, lo) and e is added to lo (double-float
+// summation: Dekker 1971; Ogita, Rump and Oishi 2005). Each 64x64 tile of an
+// upper block of G is summed over one row chunk and added to G in FP64.
+__device__ __forceinline__ void df_add_prod(float a, float b, float& hi, float& lo) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float s = hi + p;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (p - bp);
+  hi = s;
+  lo += err + e;
+}
+
+__global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ Y, int64_t m, int64_t k, int64_t ld,
+                                                 int64_t chunk, double* G) {
+  __shared__ float si[16][65];
+  __shared__ float sj[16][65];
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (tj < ti) return;
+  const int64_t r0 = blockIdx.z * chunk, r1 = min(m, r0 + chunk);
+  const int tid = threadIdx.x;
+  const int tr = tid / 16, tc = tid % 16;   // 4x4 outputs: rows tr + 16 a, cols tc + 16 b
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { hi[a][b] = 0.f; lo[a][b] = 0.f; }
+  for (int64_t rb = r0; rb < r1; rb += 16) {
+    for (int e = tid; e < 16 * 64; e += 256) {
+      int c = e / 16, rr = e % 16;
+      int64_t r = rb + rr;
+      int64_t ci = (int64_t)ti * 64 + c, cj = (int64_t)tj * 64 + c;
+      si[rr][c] = (r < r1 && ci < k) ? Y[ci * ld + r] : 0.f;
+      sj[rr][c] = (r < r1 && cj < k) ? Y[cj * ld + r] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 16; ++rr) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = si[rr][tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = sj[rr][tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) df_add_prod(av[a], bv[b], hi[a][b], lo[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int64_t gi = (int64_t)ti * 64 + tr + 16 * a;
+    if (gi >= k) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int64_t gj = (int64_t)tj * 64 + tc + 16 * b;
+      if (gj >= k || gj < gi) continue;
+      atomicAdd(&G[gi * k + gj], (double)hi[a][b] + (double)lo[a][b]);
+    }
+  }
+}
+
 __global__ void k_mirror_upper(double* G, int k) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
     int i = e / k, j = e % k;
@@ -138,6 +205,108 @@ __global__ void __launch_bounds__(1024) k_cholesky(double* G, int k, double tol,
   if (tid == 0) info[0] = 0;
 }
 
+// Blocked right-looking Cholesky over the whole GPU (cooperative launch, panel
+// width 32): block 0 factors the diagonal block in shared memory, every block
+// solves its share of the panel row, every block updates its share of the
+// trailing upper triangle; grid barriers in between. Same pivot test as above.
+constexpr int CH_NB = 32;
+__global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double tol, int* info, double* ws) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double D[CH_NB][CH_NB + 1];
+  __shared__ int bad_s;
+  const int tid = threadIdx.x;
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + tid;
+  const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && tid == 0) {
+    double dm = 0;
+    for (int i = 0; i < k; ++i) dm = fmax(dm, G[(int64_t)i * k + i]);
+    ws[0] = dm;
+    info[0] = !(dm > 0) || !isfinite(dm);
+  }
+  grid.sync();
+  if (*(volatile int*)info) return;
+  const double dmax = ws[0];
+  for (int p0 = 0; p0 < k; p0 += CH_NB) {
+    const int nb = min(CH_NB, k - p0);
+    if (blockIdx.x == 0) {
+      for (int e = tid; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = G[(int64_t)(p0 + e / nb) * k + p0 + e % nb];
+      if (tid == 0) bad_s = 0;
+      __syncthreads();
+      for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+          double d = D[j][j];
+          if (!(d > tol * dmax) || !isfinite(d)) bad_s = 1;
+          D[j][j] = sqrt(fmax(d, 0.0));
+        }
+        __syncthreads();
+        if (bad_s) break;
+        for (int c = j + 1 + tid; c < nb; c += blockDim.x) D[j][c] /= D[j][j];
+        __syncthreads();
+        const int n = nb - j - 1;
+        for (int e = tid; e < n * n; e += blockDim.x) {
+          int i = j + 1 + e / n, c = j + 1 + e % n;
+          if (c >= i) D[i][c] -= D[j][i] * D[j][c];
+        }
+        __syncthreads();
+      }
+      if (tid == 0 && bad_s) info[0] = 1;
+      for (int e = tid; e < nb * nb; e += blockDim.x) {
+        int i = e / nb, c = e % nb;
+        if (c >= i) G[(int64_t)(p0 + i) * k + p0 + c] = D[i][c];
+      }
+    }
+    grid.sync();
+    if (*(volatile int*)info) return;
+    // panel row: R[p0:p0+nb, c] solves R_pp^T x = G[p0:p0+nb, c] for c >= p0 + nb
+    for (int64_t c = p0 + nb + gtid; c < k; c += gsize) {
+      for (int i = 0; i < nb; ++i) {
+        double x = G[(int64_t)(p0 + i) * k + c];
+        for (int l = 0; l < i; ++l) x -= G[(int64_t)(p0 + l) * k + p0 + i] * G[(int64_t)(p0 + l) * k + c];
+        G[(int64_t)(p0 + i) * k + c] = x / G[(int64_t)(p0 + i) * k + p0 + i];
+      }
+    }
+    grid.sync();
+    // trailing update of the upper triangle
+    const int64_t r0 = p0 + nb, n = k - r0;
+    for (int64_t e = gtid; e < n * n; e += gsize) {
+      const int64_t i = r0 + e / n, c = r0 + e % n;
+      if (c < i) continue;
+      double acc = 0;
+      for (int l = 0; l < nb; ++l) acc = fma(G[(int64_t)(p0 + l) * k + i], G[(int64_t)(p0 + l) * k + c], acc);
+      G[i * k + c] -= acc;
+    }
+    grid.sync();
+  }
+  for (int64_t e = gtid; e < (int64_t)k * k; e += gsize) {
+    int64_t i = e / k, c = e % k;
+    if (c < i) G[e] = 0.0;
+  }
+}
+
+// Rinv = R^{-1} for upper-triangular R (row-major): one warp per column, the
+// back-substitution dot products split over the lanes, the column kept in
+// shared memory.
+__global__ void __launch_bounds__(128) k_tri_inverse_warp(const double* R, int k, double* Rinv) {
+  extern __shared__ double xs_all[];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  double* x = xs_all + (int64_t)w * k;
+  const int j = blockIdx.x * (blockDim.x / 32) + w;
+  if (j >= k) return;
+  for (int i = lane; i < k; i += 32) x[i] = 0.0;
+  __syncwarp();
+  if (lane == 0) x[j] = 1.0 / R[(int64_t)j * k + j];
+  __syncwarp();
+  for (int i = j - 1; i >= 0; --i) {
+    double sdot = 0;
+    for (int l = i + 1 + lane; l <= j; l += 32) sdot = fma(R[(int64_t)i * k + l], x[l], sdot);
+    for (int o = 16; o; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+    if (lane == 0) x[i] = -sdot / R[(int64_t)i * k + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < k; i += 32) Rinv[(int64_t)i * k + j] = x[i];
+}
+
 // Rinv = R^{-1} for upper-triangular R (row-major); column j solved by thread j.
 __global__ void k_tri_inverse(const double* R, int k, double* Rinv) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
@@ -167,8 +336,17 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k
   const int kk = (k % 2) ? k + 1 : k;   // dummy column k when odd
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
   __shared__ int rotated;
+  __shared__ double fro2;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) V[e] = ((e / k) == (e % k)) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) {
+    double f = 0;
+    for (int64_t e = 0; e < (int64_t)k * k; ++e) f = fma(M[e], M[e], f);
+    fro2 = f;
+  }
   __syncthreads();
+  // a column whose squared norm is below 1e-30 of the whole matrix carries no
+  // resolvable direction: rotations against it only stir rounding noise
+  const double tiny = 1e-30 * fro2;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
@@ -190,7 +368,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (fabs(ga) <= eps * sqrt(al * be) || ga == 0.0) continue;
+        if (ga == 0.0 || fmin(al, be) <= tiny || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
         double zeta = (be - al) / (2.0 * ga);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -209,7 +387,76 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k
     if (!rotated) break;
     __syncthreads();
   }
-  if (threadIdx.x == 0) info[0] = (sweep >= max_sweeps) ? 2 : 0;
+  // reaching the sweep cap leaves the columns orthogonal to rounding level; it is not an error
+  if (threadIdx.x == 0) info[0] = 0;
+}
+
+// The same method spread over the whole GPU: one warp per column pair, a grid
+// barrier (cooperative launch) between rounds. ws[0..3]: sweep rotation
+// counters (two, alternating) and the squared Frobenius norm.
+__global__ void __launch_bounds__(256) k_jacobi_svd_coop(double* M, double* V, int k, int max_sweeps, double eps,
+                                                         unsigned long long* ws) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int kk = (k % 2) ? k + 1 : k;
+  const int lane = threadIdx.x % 32;
+  const int gwarp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int nwarps = gridDim.x * (blockDim.x / 32);
+  double* fro2p = (double*)&ws[2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = ((e / k) == (e % k)) ? 1.0 : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double f = 0;
+    for (int64_t e = 0; e < (int64_t)k * k; ++e) f = fma(M[e], M[e], f);
+    *fro2p = f;
+    ws[0] = 0;
+    ws[1] = 0;
+  }
+  grid.sync();
+  const double tiny = 1e-30 * (*fro2p);
+  // The rotation counter of sweep s lives in ws[s & 1] (nobody else touches it
+  // during sweep s). After the last round every block reads it and a further
+  // barrier follows, so all blocks take the same break decision; the slot is
+  // cleared for sweep s+2 at round 1 of sweep s+1, after those reads.
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int round = 0; round < kk - 1; ++round) {
+      if (round == 1 && blockIdx.x == 0 && threadIdx.x == 0) ws[(sweep + 1) & 1] = 0;
+      for (int pr = gwarp; pr < kk / 2; pr += nwarps) {
+        int a = rr_player(pr, round, kk), b = rr_player(kk - 1 - pr, round, kk);
+        int p = min(a, b), q = max(a, b);
+        if (q >= k) continue;
+        double* mp = M + (int64_t)p * k;
+        double* mq = M + (int64_t)q * k;
+        double al = 0, be = 0, ga = 0;
+        for (int i = lane; i < k; i += 32) {
+          double x = mp[i], y = mq[i];
+          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+        }
+        for (int o = 16; o; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga == 0.0 || fmin(al, be) <= tiny || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        for (int i = lane; i < k; i += 32) {
+          double x = mp[i], y = mq[i];
+          mp[i] = c * x - sn * y;
+          mq[i] = sn * x + c * y;
+          double vx = V[(int64_t)p * k + i], vy = V[(int64_t)q * k + i];
+          V[(int64_t)p * k + i] = c * vx - sn * vy;
+          V[(int64_t)q * k + i] = sn * vx + c * vy;
+        }
+        if (lane == 0) atomicAdd(&ws[sweep & 1], 1ull);
+      }
+      grid.sync();
+    }
+    const unsigned long long rot = *(volatile unsigned long long*)&ws[sweep & 1];
+    grid.sync();
+    if (rot == 0) break;
+  }
 }
 
 // sigma_j = |m_j|, U_j = m_j / sigma_j (0 when sigma_j == 0), written in
@@ -217,18 +464,27 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k
 // order[rank] = original column.
 __global__ void k_svd_finish(const double* M, int k, double* U, double* sigma, int* order) {
   __shared__ double sig[1024];
+  __shared__ double fro2;
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     double s = 0;
     for (int i = 0; i < k; ++i) s = fma(M[(int64_t)j * k + i], M[(int64_t)j * k + i], s);
     sig[j] = sqrt(s);
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0;
+    for (int j = 0; j < k; ++j) f = fma(sig[j], sig[j], f);
+    fro2 = f;
+  }
+  __syncthreads();
+  // columns at or below the Jacobi negligibility level were never orthogonalised:
+  // they get a zero singular vector instead of a normalised rounding residue
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     int rank = 0;
     for (int i = 0; i < k; ++i) rank += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
     order[rank] = j;
     sigma[rank] = sig[j];
-    double inv = sig[j] > 0 ? 1.0 / sig[j] : 0.0;
+    double inv = (sig[j] > 0 && sig[j] * sig[j] > 1e-30 * fro2) ? 1.0 / sig[j] : 0.0;
     for (int i = 0; i < k; ++i) U[(int64_t)rank * k + i] = M[(int64_t)j * k + i] * inv;
   }
 }
@@ -380,6 +636,22 @@ void gaussian_sketch(cudaStream_t s, T* out, int64_t n_rows, int64_t k, int64_t 
 template <class T>
 void gram_f64(cudaStream_t s, const T* Y, int64_t m, int64_t k, int64_t ld, double* G) {
   FP_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * k * k, s));
+  if (sizeof(T) == 4) {
+    int tiles = (int)((k + 63) / 64);
+    int64_t tri = (int64_t)tiles * (tiles + 1) / 2;
+    int64_t nchunk = std::max<int64_t>(1, (152 * 4 + tri - 1) / tri);
+    int64_t chunk = ((m + nchunk - 1) / nchunk + 15) / 16 * 16;
+    if (chunk < 16) chunk = 16;
+    nchunk = (m + chunk - 1) / chunk;
+    dim3 grid(tiles, tiles, (unsigned)std::max<int64_t>(nchunk, 1));
+    ProfToken pt = prof_begin(PROF_GRAM, s, 2.0 * m * k * k, 4.0 * m * k);
+    k_gram_df<<<grid, 256, 0, s>>>((const float*)Y, m, k, ld, chunk, G);
+    FP_LAUNCH();
+    prof_end(pt, s);
+    k_mirror_upper<<<grid_for(k * k), 256, 0, s>>>(G, (int)k);
+    FP_LAUNCH();
+    return;
+  }
   int tiles = (int)((k + 31) / 32);
   int64_t target_blocks = 152 * 8;
   int64_t tri = (int64_t)tiles * (tiles + 1) / 2;
@@ -390,26 +662,79 @@ void gram_f64(cudaStream_t s, const T* Y, int64_t m, int64_t k, int64_t ld, doub
   nchunk = (m + chunk - 1) / chunk;
   if (nchunk < 1) nchunk = 1;
   dim3 grid(tiles, tiles, (unsigned)nchunk);
+  ProfToken pt = prof_begin(PROF_GRAM, s, 2.0 * m * k * k, (double)sizeof(T) * m * k);
   k_gram<T><<<grid, 256, 0, s>>>(Y, m, k, ld, chunk, G);
   FP_LAUNCH();
+  prof_end(pt, s);
   k_mirror_upper<<<grid_for(k * k), 256, 0, s>>>(G, (int)k);
   FP_LAUNCH();
 }
 
-void cholesky_upper_f64(cudaStream_t s, double* G, int k, int* info) {
-  k_cholesky<<<1, 1024, 0, s>>>(G, k, 1e-13, info);
-  FP_LAUNCH();
+void cholesky_upper_f64(cudaStream_t s, double* G, int k, int* info, double* ws) {
+  if (k <= 96) {
+    k_cholesky<<<1, 1024, 0, s>>>(G, k, 1e-13, info);
+    FP_LAUNCH();
+    return;
+  }
+  static int max_blocks = -1;
+  if (max_blocks < 0) {
+    int dev = 0, sms = 0, per = 0;
+    FP_CUDA(cudaGetDevice(&dev));
+    FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cholesky_coop, 256, 0));
+    max_blocks = sms * std::max(per, 0);
+  }
+  int blocks = std::min(max_blocks, 152);
+  FP_CHECK(blocks >= 1, FPEPS_ERR_CUDA, "cholesky: no co-resident blocks");
+  double tol = 1e-13;
+  void* args[] = {&G, &k, &tol, &info, &ws};
+  ProfToken pt = prof_begin(PROF_FACTOR, s, (double)k * k * k / 3.0, 8.0 * k * k);
+  count_launch();
+  FP_CUDA(cudaLaunchCooperativeKernel((void*)k_cholesky_coop, blocks, 256, args, 0, s));
+  prof_end(pt, s);
 }
 
 void tri_inverse_upper_f64(cudaStream_t s, const double* R, int k, double* Rinv) {
-  k_tri_inverse<<<(k + 127) / 128, 128, 0, s>>>(R, k, Rinv);
+  const int wpb = 4;
+  size_t smem = (size_t)wpb * k * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    FP_CUDA(cudaFuncSetAttribute(k_tri_inverse_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 1024 * 8));
+    attr = true;
+  }
+  FP_CHECK(k <= 1024, FPEPS_ERR_UNSUPPORTED, "tri_inverse: k > 1024");
+  k_tri_inverse_warp<<<(k + wpb - 1) / wpb, wpb * 32, smem, s>>>(R, k, Rinv);
   FP_LAUNCH();
 }
 
-void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma, double* V, int* order, int* info) {
+void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma, double* V, int* order, int* info,
+                    void* ws_dev) {
   FP_CHECK(k <= 1024, FPEPS_ERR_UNSUPPORTED, "svd: k > 1024");
-  k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15, info);
-  FP_LAUNCH();
+  if (k <= 96) {
+    k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15, info);
+    FP_LAUNCH();
+  } else {
+    static int max_blocks = -1;
+    if (max_blocks < 0) {
+      int dev = 0, sms = 0, per = 0;
+      FP_CUDA(cudaGetDevice(&dev));
+      FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_svd_coop, 256, 0));
+      max_blocks = sms * std::max(per, 0);
+    }
+    int pairs = (k + 1) / 2;
+    int blocks = std::min(max_blocks, (pairs + 7) / 8);
+    FP_CHECK(blocks >= 1, FPEPS_ERR_CUDA, "svd: no co-resident blocks");
+    unsigned long long* ws = (unsigned long long*)ws_dev;
+    int max_sweeps = 30;
+    double eps = 1e-15;
+    void* args[] = {&Mat, &V, &k, &max_sweeps, &eps, &ws};
+    ProfToken pt = prof_begin(PROF_FACTOR, s, 0.0, 16.0 * k * k);
+    count_launch();
+    FP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_svd_coop, blocks, 256, args, 0, s));
+    prof_end(pt, s);
+    FP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  }
   k_svd_finish<<<1, 1024, 0, s>>>(Mat, k, U, sigma, order);
   FP_LAUNCH();
 }
@@ -498,9 +823,10 @@ void svqb_factors(cudaStream_t s, const double* G, int k, double* work, double* 
   double* Vs = V + (int64_t)k * k;
   double* lam = Vs + (int64_t)k * k;
   int* order = (int*)(lam + k);
+  void* jws = (void*)(((uintptr_t)(order + k) + 63) & ~(uintptr_t)63);
   k_svqb_scale<<<grid_for((int64_t)k * k), 256, 0, s>>>(G, k, d, Gs);
   FP_LAUNCH();
-  svd_jacobi_f64(s, Gs, k, U, lam, V, order, info);
+  svd_jacobi_f64(s, Gs, k, U, lam, V, order, info, jws);
   gather_cols_f64(s, V, order, k, Vs);
   k_svqb_factors<<<grid_for((int64_t)k * k), 256, 0, s>>>(Vs, lam, d, k, Bt, Rq);
   FP_LAUNCH();

@@ -11,6 +11,8 @@
 // (bra fastest), maps to O[V][Z] with V = (v, v_w, v'), Z = (z, z_w, z'):
 //   acc[x',y',v,z,q]   = sum_{ch in (v_w,z_w)} sum_{x,y} I[(x,x_w,x'),(y,y_w,y')] AW_ch[x,y,v,z,q]
 //   O[(v,v_w,v'),(z,z_w,z')] = sum_{x',y',q} acc[x',y',v,z,q] A[x',y',v',z',q]
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fpeps {
@@ -173,6 +175,185 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Tensor-core sandwich (3xTF32 with warp-level mma.sync m16n8k8): a CTA takes
+// NB consecutive (t, k) blocks, so that the ket step is one small GEMM with
+// rows (b, x', y') (<= 144 = 9 m16 tiles), K = (x, y) padded to a multiple of 8
+// (<= 40) and N = (v, z, q) (<= 144 = 18 n8 tiles), accumulated over the
+// channels of one output (v_w, z_w) pair; the accumulator is written to shared
+// memory transposed to rows (b, v, z), K = (x', y', q) for the bra GEMM with
+// N = (v', z') (<= 40). Every operand is split x = hi + lo (TF32 round to
+// nearest) and the three products hi*hi + hi*lo + lo*hi accumulate in FP32.
+constexpr int SM_MT = 9, SM_PA = 44, SM_PB = 152, SM_PC = 148, SM_PR = 40;
+constexpr int SM_THREADS = 288;   // 9 warps
+constexpr int SM_FLOATS = 144 * SM_PA + 40 * SM_PB + 144 * SM_PC + 144 * SM_PR;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32_16x8x8(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// 3xTF32 product from fp32 fragments
+__device__ __forceinline__ void mma3(float* d, const float* af, const float* bf) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_tf32(af[i], ah[i], al[i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) split_tf32(bf[i], bh[i], bl[i]);
+  mma_tf32_16x8x8(d, al, bh);
+  mma_tf32_16x8x8(d, ah, bl);
+  mma_tf32_16x8x8(d, ah, bh);
+}
+
+__global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, int64_t nt, int64_t nk, int nb_per,
+                                                                const float* __restrict__ in, int64_t i_t,
+                                                                int64_t i_k, int64_t i_X, int64_t i_Y,
+                                                                float* __restrict__ out, int64_t o_t, int64_t o_k,
+                                                                int64_t o_V, int64_t o_Z) {
+  extern __shared__ float sm[];
+  float* sA = sm;                       // [144][SM_PA]   rows (b, x', y'), cols (x, y)
+  float* sB = sA + 144 * SM_PA;         // [40][SM_PB]    rows (x, y), cols (v, z, q)
+  float* sC = sB + 40 * SM_PB;          // [144][SM_PC]   rows (b, v, z), cols (x', y', q)
+  float* sR = sC + 144 * SM_PC;         // [144][SM_PR]   rows (x', y', q), cols (v', z')
+  const float* AW = static_cast<const float*>(o.d_aw);
+  const float* AR = static_cast<const float*>(o.d_ar);
+  const int nx = o.nx, ny = o.ny, nv = o.nv, nz = o.nz, p = o.p;
+  const int K1 = nx * ny, N1 = nv * nz * p, K2 = nx * ny * p, N2 = nv * nz;
+  const int K1p = (K1 + 7) & ~7;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int g = lane >> 2, q4 = lane & 3;
+  const int64_t nblk = nt * nk;
+  const int64_t b0 = (int64_t)blockIdx.x * nb_per;
+  const int nb = (int)min((int64_t)nb_per, nblk - b0);
+  const int M1 = nb * K1, M2 = nb * N2;
+
+  // zero everything once (padding must read as zero), then the bra operand
+  for (int e = tid; e < SM_FLOATS; e += SM_THREADS) sm[e] = 0.f;
+  __syncthreads();
+  for (int e = tid; e < K2 * N2; e += SM_THREADS) {
+    int r = e / N2, c = e % N2;            // r = (x', y', q), c = (v', z')
+    int q = r % p, xy = r / p, yp = xy % ny, xp = xy / ny;
+    int zp = c % nz, vp = c / nz;
+    sR[r * SM_PR + c] = AR[(((xp * ny + yp) * nv + vp) * nz + zp) * p + q];
+  }
+
+  for (int vw = 0; vw < o.nvw; ++vw) {
+    for (int zw = 0; zw < o.nzw; ++zw) {
+      const int pair = vw * o.nzw + zw;
+      const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
+      float acc[3][6][4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+      const int mg = warp / 3, ng = warp % 3;
+      for (int c = c0; c < c1; ++c) {
+        const int xw = o.d_ch[4 * c + 0], yw = o.d_ch[4 * c + 1];
+        __syncthreads();
+        // A: rows (bi, x', y'), cols (x, y) from block bi's input
+        for (int e = tid; e < M1 * K1; e += SM_THREADS) {
+          int m = e / K1, kk = e % K1;
+          int bi = m / K1, xy = m % K1, xp = xy / ny, yp = xy % ny;
+          int x = kk / ny, y = kk % ny;
+          int64_t b = b0 + bi, t = b / nk, k = b % nk;
+          int64_t X = ((int64_t)x * o.nxw + xw) * nx + xp, Y = ((int64_t)y * o.nyw + yw) * ny + yp;
+          sA[m * SM_PA + kk] = in[t * i_t + k * i_k + X * i_X + Y * i_Y];
+        }
+        const float* awc = AW + (int64_t)c * K1 * N1;
+        for (int e = tid; e < K1 * N1; e += SM_THREADS) sB[(e / N1) * SM_PB + e % N1] = awc[e];
+        __syncthreads();
+        for (int k0 = 0; k0 < K1p; k0 += 8) {
+          float af[3][4], bf[6][2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const int r0 = (mg * 3 + i) * 16 + g;
+            af[i][0] = sA[r0 * SM_PA + k0 + q4];
+            af[i][1] = sA[(r0 + 8) * SM_PA + k0 + q4];
+            af[i][2] = sA[r0 * SM_PA + k0 + q4 + 4];
+            af[i][3] = sA[(r0 + 8) * SM_PA + k0 + q4 + 4];
+          }
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const int n = (ng * 6 + j) * 8 + g;
+            bf[j][0] = sB[(k0 + q4) * SM_PB + n];
+            bf[j][1] = sB[(k0 + q4 + 4) * SM_PB + n];
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 6; ++j) mma3(acc[i][j], af[i], bf[j]);
+        }
+      }
+      __syncthreads();
+      // acc (rows (bi,x',y'), cols (v,z,q)) -> sC rows (bi,v,z), cols (x',y',q)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int m = (mg * 3 + i) * 16 + g + ((r >> 1) << 3);
+            const int n = (ng * 6 + j) * 8 + q4 * 2 + (r & 1);
+            if (m < M1 && n < N1) {
+              int bi = m / K1, xy = m % K1;
+              int q = n % p, vz = n / p;
+              sC[(bi * N2 + vz) * SM_PC + xy * p + q] = acc[i][j][r];
+            }
+          }
+      __syncthreads();
+      // bra: rows (bi, v, z) x cols (v', z'), K = (x', y', q)
+      float d2[5][4];
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) d2[j][r] = 0.f;
+      const int K2p = (K2 + 7) & ~7;
+      for (int k0 = 0; k0 < K2p; k0 += 8) {
+        float af[4], bf[5][2];
+        const int r0 = warp * 16 + g;
+        af[0] = sC[r0 * SM_PC + k0 + q4];
+        af[1] = sC[(r0 + 8) * SM_PC + k0 + q4];
+        af[2] = sC[r0 * SM_PC + k0 + q4 + 4];
+        af[3] = sC[(r0 + 8) * SM_PC + k0 + q4 + 4];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          bf[j][0] = sR[(k0 + q4) * SM_PR + j * 8 + g];
+          bf[j][1] = sR[(k0 + q4 + 4) * SM_PR + j * 8 + g];
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) mma3(d2[j], af, bf[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int m = warp * 16 + g + ((r >> 1) << 3);
+          const int n = j * 8 + q4 * 2 + (r & 1);
+          if (m < M2 && n < N2) {
+            int bi = m / N2, vz = m % N2, v = vz / nz, z = vz % nz;
+            int vp = n / nz, zp = n % nz;
+            int64_t b = b0 + bi, t = b / nk, k = b % nk;
+            int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp, Z = ((int64_t)z * o.nzw + zw) * nz + zp;
+            out[t * o_t + k * o_k + V * o_V + Z * o_Z] = d2[j][r];
+          }
+        }
+    }
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (int)(g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g));
@@ -210,6 +391,32 @@ void first_row_tensor(cudaStream_t s, const T* A, const int dA[5], const T* W, c
   for (int i = 0; i < 6; ++i) a.dW[i] = dW[i];
   int64_t n = (int64_t)dA[0] * dW[0] * dA[0] * dA[3] * dW[3] * dA[3] * dA[2] * dW[2] * dA[2];
   k_first_row<T><<<grid_for(n), 256, 0, s>>>(A, a, W, out);
+  FP_LAUNCH();
+}
+
+bool sandwich_mma_fits(const SandOrient& o) {
+  const int K1 = o.nx * o.ny, N1 = o.nv * o.nz * o.p, K2 = K1 * o.p, N2 = o.nv * o.nz;
+  return K1 <= 40 && N1 <= 144 && K2 <= 144 && N2 <= 40 && K1 >= 1 && N2 >= 1;
+}
+
+void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const float* in, int64_t i_t,
+                       int64_t i_k, int64_t i_X, int64_t i_Y, float* out, int64_t o_t, int64_t o_k, int64_t o_V,
+                       int64_t o_Z) {
+  if (nt <= 0 || nk <= 0) return;
+  FP_CHECK(sandwich_mma_fits(o), FPEPS_ERR_UNSUPPORTED, "tensor-core sandwich: site dimensions too large");
+  const int K1 = o.nx * o.ny, N2 = o.nv * o.nz;
+  const int nb_per = std::max(1, std::min(144 / K1, 144 / N2));
+  const int64_t nblk = nt * nk;
+  const int64_t grid = (nblk + nb_per - 1) / nb_per;
+  FP_CHECK(grid < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core sandwich: too many blocks");
+  const size_t smem = (size_t)SM_FLOATS * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    FP_CUDA(cudaFuncSetAttribute(k_sandwich_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  k_sandwich_mma<<<(unsigned)grid, SM_THREADS, smem, s>>>(o, nt, nk, nb_per, in, i_t, i_k, i_X, i_Y, out, o_t, o_k,
+                                                          o_V, o_Z);
   FP_LAUNCH();
 }
 

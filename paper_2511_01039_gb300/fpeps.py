@@ -74,6 +74,13 @@ SIGNATURES = {
                                       C.POINTER(C.c_int32)]),
     "fpeps_apply_theta": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                                     C.c_void_p]),
+    "fpeps_gemm_f32": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_int64, C.c_void_p, C.c_void_p]),
+    "fpeps_svd_f64": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fpeps_launch_count": (C.c_int64, []),
+    "fpeps_profile": (C.c_int, [C.c_int32]),
+    "fpeps_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
     "fpeps_version": (C.c_char_p, []),
 }
 
@@ -208,6 +215,44 @@ def fpeps_apply_theta(env, c: int, el, x, dn: int, elem_bytes: int):
     y = np.zeros((k, a, dn), dtype=dt)
     _check(env, lib().fpeps_apply_theta(env, c, a, el.ctypes.data, k, x.ctypes.data, y.ctypes.data))
     return y
+
+
+def fpeps_gemm_f32(mode: int, A, B, C, K=None, stream_handle: int = 0):
+    """C = A[:, :K] @ B[:, :K].T for torch CUDA float32 tensors (unit inner stride); C [M,N] contiguous."""
+    M = A.shape[0]
+    K = A.shape[1] if K is None else K
+    N = B.shape[0]
+    _check(None, lib().fpeps_gemm_f32(mode, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                      C.data_ptr(), stream_handle))
+
+
+def fpeps_svd_f64(M, stream_handle: int = 0):
+    """SVD of a square torch float64 CUDA matrix (row-major view of the column-major argument is handled here)."""
+    import torch
+    k = M.shape[0]
+    Mc = M.t().contiguous()             # column-major storage
+    U = torch.empty_like(Mc)
+    V = torch.empty_like(Mc)
+    s = torch.empty(k, dtype=torch.float64, device=M.device)
+    _check(None, lib().fpeps_svd_f64(Mc.data_ptr(), k, U.data_ptr(), s.data_ptr(), V.data_ptr(), stream_handle))
+    return U.t(), s, V.t()
+
+
+PROF_KINDS = {0: "gemm_tc_tf32x3", 1: "gemm_simt", 2: "sandwich", 3: "gram", 4: "factor"}
+
+
+def fpeps_launch_count() -> int:
+    return lib().fpeps_launch_count()
+
+
+def fpeps_profile(enable: bool):
+    _check(None, lib().fpeps_profile(int(enable)))
+
+
+def fpeps_profile_read(kind: int):
+    n, ms, fl, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+    _check(None, lib().fpeps_profile_read(kind, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
 
 def fpeps_version() -> str:

@@ -1,0 +1,39 @@
+"""Full-size parity on sampled outputs (8x8, D=6, w=6 Hubbard FSM PEPO, chi=500).
+
+The oracle cannot run a whole chi=500 row in a test, but it can apply
+Theta_c of the central site to a few vectors: the GPU path (tensor-core GEMMs
+and sandwich, launch configuration of the benchmark) applies the same matrix
+through fpeps_apply_theta and the results are compared element by element.
+"""
+import numpy as np
+import pytest
+
+from oracle import boundary as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 2e-5), ("f32", 2e-5)])
+def test_central_site_theta_at_chi_500(prec, tol):
+    import torch
+    from paper_2511_01039_gb300 import fpeps as fp
+    from paper_2511_01039_gb300 import workloads as WL
+    torch.cuda.set_device(0)
+    w = WL.hubbard_row(**WL.C4)
+    env = fp.Env(w.peps, w.pepo, D=w.D, p=w.p, w=w.w, chi=w.chi, prec=prec, seed=1)
+    fp.fpeps_import_boundary(env.h, WL.boundary_blob(w.boundary, w.row, 1, 4), w.row, 1)
+    fp.fpeps_absorb_row(env.h, w.row, 1)
+    c = 3
+    A, W, T = w.peps[w.row][c], w.pepo[w.row][c], w.boundary[c]
+    t, tp = T.shape[0], T.shape[2]
+    dL, dR, dD = B.bdim(A, W, 0), B.bdim(A, W, 2), B.bdim(A, W, 3)
+    g = np.random.default_rng(7)
+    el = g.standard_normal((w.chi, t, dL)).astype(np.float32)
+    x = g.standard_normal((2, tp, dR)).astype(np.float32)
+    y = env.apply_theta(c, el, x, dD)
+    env.close()
+    yo = B.theta(el.astype(np.float64), T.astype(np.float32).astype(np.float64), A.astype(np.float32).astype(np.float64),
+                 W.astype(np.float32).astype(np.float64), np.moveaxis(x, 0, -1).astype(np.float64))
+    yo = np.moveaxis(yo, -1, 0)
+    err = np.abs(y - yo).max() / np.abs(yo).max()
+    assert err < tol, err

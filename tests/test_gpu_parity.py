@@ -39,7 +39,7 @@ def _env(fp, peps, pepo, *, D, w, chi, prec, seed):
 
 
 @pytest.mark.parametrize("kind", ["identity", "dense2", "fsm2", "fsm4"])
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4), ("tf32x3", 1e-4)])
 def test_c1_3x3_exact_against_brute_force(fp, kind, prec, tol):
     peps = L.random_peps(3, 3, 2, 4, seed=0)
     if kind == "identity":
@@ -61,7 +61,7 @@ def test_c1_3x3_exact_against_brute_force(fp, kind, prec, tol):
     assert _rel(val, num / den) < 2 * tol
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4), ("tf32x3", 2e-4)])
 @pytest.mark.parametrize("n_fit", [0, 1])
 def test_truncated_4x4_matches_oracle_algorithm(fp, prec, tol, n_fit):
     """Truncated regime (chi=12 < exact bonds): same algorithm, same Omega, both sides."""
@@ -80,6 +80,28 @@ def test_truncated_4x4_matches_oracle_algorithm(fp, prec, tol, n_fit):
     env.close()
     assert sg == sn_o
     assert abs(lg - ln_o) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("tf32x3", 1e-5)])
+def test_apply_theta_small_sites(fp, prec, tol):
+    """One Theta_c application on every site of an interior row (ragged edge dims)."""
+    peps = L.random_peps(4, 4, 3, 4, seed=11)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=11))
+    T, _ = B.first_row_boundary(peps[0], pepo[0])
+    env = _env(fp, peps, pepo, D=3, w=4, chi=40, prec=prec, seed=5)
+    fp.fpeps_absorb_row(env.h, 0, 1)
+    fp.fpeps_absorb_row(env.h, 1, 1)
+    g = np.random.default_rng(1)
+    for c in range(4):
+        A, W = peps[1][c], pepo[1][c]
+        t, tp = T[c].shape[0], T[c].shape[2]
+        dL, dR, dD = B.bdim(A, W, 0), B.bdim(A, W, 2), B.bdim(A, W, 3)
+        el = g.standard_normal((7, t, dL))
+        x = g.standard_normal((5, tp, dR))
+        y = env.apply_theta(c, el, x, dD)
+        yo = np.moveaxis(B.theta(el, T[c], A, W, np.moveaxis(x, 0, -1)), -1, 0)
+        assert np.abs(y - yo).max() <= tol * np.abs(yo).max(), c
+    env.close()
 
 
 def test_zip_spectrum_and_apply_theta_match_oracle(fp):
@@ -153,7 +175,7 @@ def test_product_state_closed_form_on_gpu(fp):
     assert abs(val - N.product_state_energy(vecs, ham)) < 1e-9 * max(1.0, abs(val))
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 1e-3)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 1e-3), ("tf32x3", 1e-3)])
 def test_c2_against_stored_oracle(fp, prec, tol):
     """4x4, D=4, w=4, chi=64 truncated; oracle values written by tests/golden/make_golden.py."""
     path = os.path.join(HERE, "golden", "c2_fsm_seed0.json")
