@@ -111,7 +111,8 @@ typedef struct fpeps_env fpeps_env;
  * The inputs are copied (and converted to the compute precision) before the
  * call returns; the caller keeps ownership of its buffers.
  * Errors: FPEPS_ERR_ARG (bad sizes/pointers), FPEPS_ERR_OOM, FPEPS_ERR_CUDA,
- * FPEPS_ERR_UNSUPPORTED (symmetry != 0 or n_envs != 1). */
+ * FPEPS_ERR_UNSUPPORTED (symmetry != 0, n_envs != 1, or prec == FPEPS_BF16X3,
+ * whose kernels are not built). */
 fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, const void* pepo_dev,
                               const int32_t* charges_host, int32_t dtype_in, void* cuda_stream,
                               const fpeps_allocator* alloc, fpeps_env** out);
@@ -196,6 +197,9 @@ fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const
  * M (k x k, column-major, device, not modified) = U diag(sigma) V^T with sigma
  * descending and U, V column-major k x k (device). Columns whose singular value
  * is below 1e-15 of the Frobenius norm get a zero U column. 1 <= k <= 1024.
+ * The path passes the transposed triangular factor of a QR, for which the
+ * method converges in about ten sweeps; the sweep count is capped at 30, so a
+ * badly conditioned general matrix may return before full convergence.
  * Allocates its scratch (2 k^2 doubles) with cudaMallocAsync on `cuda_stream`
  * and synchronises it. */
 fpeps_status fpeps_svd_f64(const double* M, int32_t k, double* U, double* sigma, double* V, void* cuda_stream);

@@ -234,6 +234,7 @@ fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, con
   if (dtype_in != 0 && dtype_in != 1) return FPEPS_ERR_ARG;
   if (c.Ly > 4096 || c.Lx > 4096 || c.D > 64 || c.p > 64 || c.w > 64) return FPEPS_ERR_ARG;
   if (c.symmetry != 0 || c.n_envs != 1 || charges_host) return FPEPS_ERR_UNSUPPORTED;
+  if (c.prec == FPEPS_BF16X3) return FPEPS_ERR_UNSUPPORTED;   // 3xBF16 kernels are not built
   fpeps_env* env = new (std::nothrow) fpeps_env();
   if (!env) return FPEPS_ERR_OOM;
   env->cfg = c;
@@ -515,10 +516,11 @@ fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const
     if (mode != FPEPS_TF32X3) throw Error{FPEPS_ERR_UNSUPPORTED, "mode"};
     if (!fpeps::gemm_tc_supported(M, N, K, lda, ldb) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16))
       throw Error{FPEPS_ERR_UNSUPPORTED, "shape not supported by the tensor-core kernel"};
+    const size_t sb = fpeps::gemm_tc_scratch_bytes(mode, M, N, K);
     int* err = nullptr;
-    FP_CUDA(cudaMallocAsync((void**)&err, 256, s));
+    FP_CUDA(cudaMallocAsync((void**)&err, sb, s));
     FP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    fpeps::gemm_tc(s, mode, M, N, K, A, lda, B, ldb, C, om, err, 256);
+    fpeps::gemm_tc(s, mode, M, N, K, A, lda, B, ldb, C, om, err, sb);
     int h = 0;
     FP_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FP_CUDA(cudaStreamSynchronize(s));

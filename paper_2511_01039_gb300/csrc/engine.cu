@@ -179,7 +179,10 @@ struct Engine : EngineBase {
         ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0) {
       size_t need = gemm_tc_scratch_bytes(mode, M, N, K);
       if (!tc_scr || tc_n < need) {
-        if (tc_scr) env->al.put(tc_scr);
+        if (tc_scr) {
+          check_tc();   // keep a recorded timeout before the error word is replaced
+          env->al.put(tc_scr);
+        }
         tc_scr = env->al.get(std::max<size_t>(need, 256));
         tc_n = std::max<size_t>(need, 256);
         FP_CUDA(cudaMemsetAsync(tc_scr, 0, sizeof(int), s));

@@ -9,15 +9,27 @@
 // FP32 accumulation in TMEM:
 //   mode 2 (3xTF32): hi = x rounded to TF32 (10-bit mantissa), lo = x - hi,
 //                    kind::tf32 MMAs on the 32-bit tiles.
-// One CTA computes a BM x BN tile. Warp roles: warp 0 issues TMA loads, warp 1
-// allocates TMEM and issues MMAs (one elected thread), warps 2-7 split each
-// landed stage into hi/lo tiles (in place + a second buffer, the swizzled
-// layout is preserved element by element), warps 4-7 then drain TMEM and store
-// C through the caller's output map. Every wait on an mbarrier is bounded: a
-// timeout sets an error word, the CTA stops issuing work, waits (bounded) for
-// what it has in flight, frees its TMEM and exits.
+// The kernel is persistent (one CTA per SM walks a static tile schedule) with
+// warp roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
+// MMAs (one thread), warps 2-7 split each landed stage into hi/lo tiles (in
+// place + a second buffer; the swizzled layout is preserved element by element),
+// warps 8-11 drain TMEM and store C through the caller's output map.
+//
+// Accumulation: the tensor cores' FP32 accumulation over long K loses far more
+// than round-to-nearest FP32 (measured ~1e-5 relative at K = 2048, ~1e-3 at
+// K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 128 terms; each
+// chunk accumulates in a fresh TMEM buffer (two buffers, so the MMAs of chunk
+// i+1 overlap the drain of chunk i) and the epilogue warps fold it into a
+// compensated running sum (hi, lo) kept in the other half of TMEM (Knuth's
+// two-sum). Few output tiles are additionally split over K across CTAs, with
+// the partials summed in FP64.
+//
+// Every wait on an mbarrier is bounded: a timeout sets an error word, the CTA
+// stops issuing work, waits (bounded) for what it has in flight, frees its
+// TMEM and exits; CTAs that start after an error return at once.
 #include <cuda.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -29,9 +41,7 @@ constexpr int BM = 128, BN = 128, BK = 32;   // BK fp32 = 128 bytes = one 128B s
 constexpr int STAGES = 3;
 constexpr int TILE_A = BM * BK * 4, TILE_B = BN * BK * 4;       // bytes
 constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);               // hi + lo of A and B
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int NTHREADS = 256;
-constexpr int CONV_WARP0 = 2, N_CONV_WARPS = 6;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;   // tiles + barriers + slack
 constexpr unsigned long long WAIT_LIMIT = 2000000000ull;   // clock64 cycles (~1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -97,6 +107,36 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 __device__ __forceinline__ uint32_t tf32_round(uint32_t bits) { return (bits + 0x1000u) & 0xFFFFE000u; }
 
+// 32 consecutive TMEM columns of this thread's lane (32x32b shape)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])),
+      "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])),
+      "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
 struct TcArgs {
   int64_t M, N, K;
   OutMap om;
@@ -104,46 +144,69 @@ struct TcArgs {
   int* err;
   int m_fast;   // rasterisation: 1 => consecutive blocks walk m
   int64_t mt, nt;
+  int ks;       // k-blocks per K slice (split-K); nsplit = ceil(nk / ks)
+  int nsplit;
+  int kch;      // k-blocks per TMEM accumulation chunk
+  float* part;  // nsplit > 1: partial results [nsplit][M][N] row-major
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tf32x3(const __grid_constant__ CUtensorMap mapA,
-                                                             const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+// Persistent variant: one CTA per SM walks the tiles tile = blockIdx.x + i*gridDim.x.
+// Two TMEM accumulators (2 x BN columns) let the epilogue warps drain tile i
+// while the MMA thread computes tile i+1. Warps: 0 TMA, 1 TMEM + MMA,
+// 2..7 hi/lo converters, 8..11 epilogue (TMEM lane quarters 0..3).
+constexpr int P_THREADS = 384, P_CONV0 = 2, P_NCONV = 6, P_EPI0 = 8;
+
+__global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_constant__ CUtensorMap mapA,
+                                                                const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+  if (*(volatile int*)g.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* conv = full + STAGES;
   uint64_t* empty = conv + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* accf = empty + STAGES;
+  uint64_t* acce = accf + 2;
+  uint64_t* drain = acce + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
-  // once any CTA has timed out, later CTAs do nothing (before touching TMEM or TMA)
-  if (*(volatile int*)g.err) return;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t bid = blockIdx.x;
-  const int64_t mt = g.m_fast ? bid % g.mt : bid / g.nt;
-  const int64_t ntile = g.m_fast ? bid / g.mt : bid % g.nt;
-  const int64_t m0 = mt * BM, n0 = ntile * BN;
-  const int nk = (int)((g.K + BK - 1) / BK);
-
+  const int64_t ntiles = g.mt * g.nt * g.nsplit;
+  const int nk_all = (int)((g.K + BK - 1) / BK);
+  auto kslice = [&](int64_t tile, int& kb0, int& nk) {
+    const int split = (int)(tile / (g.mt * g.nt));
+    kb0 = split * g.ks;
+    nk = min(g.ks, nk_all - kb0);
+  };
   auto A_hi = [&](int s) { return smem + s * STAGE_BYTES; };
   auto B_hi = [&](int s) { return smem + s * STAGE_BYTES + TILE_A; };
   auto A_lo = [&](int s) { return smem + s * STAGE_BYTES + TILE_A + TILE_B; };
   auto B_lo = [&](int s) { return smem + s * STAGE_BYTES + 2 * TILE_A + TILE_B; };
+  auto tile_mn = [&](int64_t tile, int64_t& m0, int64_t& n0) {
+    tile %= g.mt * g.nt;
+    const int64_t mt = g.m_fast ? tile % g.mt : tile / g.nt;
+    const int64_t nt = g.m_fast ? tile / g.mt : tile % g.nt;
+    m0 = mt * BM;
+    n0 = nt * BN;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], N_CONV_WARPS);
+      mbar_init(&conv[s], P_NCONV);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN));
+                 "r"(4 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -151,103 +214,161 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tf32x3(const __grid_consta
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  int issued = 0;   // stages loaded by the producer (warp 0, lane 0)
+  int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % STAGES;
-        if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag)) break;
-        mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
-        tma_load_2d(A_hi(s), &mapA, &full[s], it * BK, (int)m0);
-        tma_load_2d(B_hi(s), &mapB, &full[s], it * BK, (int)n0);
-        ++issued;
+      int it = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int64_t m0, n0;
+        tile_mn(tile, m0, n0);
+        int kb0, nk;
+        kslice(tile, kb0, nk);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
+          mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
+          tma_load_2d(A_hi(s), &mapA, &full[s], (kb0 + kb) * BK, (int)m0);
+          tma_load_2d(B_hi(s), &mapB, &full[s], (kb0 + kb) * BK, (int)n0);
+          ++issued;
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // instruction descriptor: D f32, A/B tf32, both K-major, N>>3 at bit 17, M>>4 at bit 24
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      int it = 0, lc = 0;
       bool ok = true;
-      for (int it = 0; it < nk && ok; ++it) {
-        const int s = it % STAGES;
-        if (!mbar_wait(&conv[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ah = sdesc(A_hi(s)), bh = sdesc(B_hi(s)), al = sdesc(A_lo(s)), bl = sdesc(B_lo(s));
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int kb0, nk;
+        kslice(tile, kb0, nk);
+        for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
+          const int buf = lc & 1;
+          if (!mbar_wait(&acce[buf], ((lc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(buf * BN);
+          const int c1 = min(nk, c0 + g.kch);
+          for (int kb = c0; kb < c1; ++kb, ++it) {
+            const int s = it % STAGES;
+            if (!mbar_wait(&conv[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t ah = sdesc(A_hi(s)), bh = sdesc(B_hi(s)), al = sdesc(A_lo(s)), bl = sdesc(B_lo(s));
 #pragma unroll
-        for (int kk = 0; kk < BK / 8; ++kk) {   // 8 tf32 = 32 bytes per MMA
-          const uint64_t o = (uint64_t)(kk * 32) >> 4;
-          mma_tf32(tmem, al + o, bh + o, idesc, (it | kk) ? 1u : 0u);
-          mma_tf32(tmem, ah + o, bl + o, idesc, 1u);
-          mma_tf32(tmem, ah + o, bh + o, idesc, 1u);
+            for (int kk = 0; kk < BK / 8; ++kk) {
+              const uint64_t o = (uint64_t)(kk * 32) >> 4;
+              mma_tf32(d, al + o, bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
+              mma_tf32(d, ah + o, bl + o, idesc, 1u);
+              mma_tf32(d, ah + o, bh + o, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+          }
+          if (ok) mma_commit(&accf[buf]);
         }
-        mma_commit(&empty[s]);
       }
-      mma_commit(done);
+      // every MMA issued by this thread has completed once `drain` fires
+      mma_commit(drain);
+      const unsigned long long t0 = clock64();
+      while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
+      }
+    }
+  } else if (warp < P_CONV0 + P_NCONV) {
+    const int cw = warp - P_CONV0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int kb0, nk;
+      kslice(tile, kb0, nk);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+        uint4* ah = (uint4*)A_hi(s);
+        uint4* bh = (uint4*)B_hi(s);
+        uint4* alo = (uint4*)A_lo(s);
+        uint4* blo = (uint4*)B_lo(s);
+        for (int e = cw * 32 + lane; e < (TILE_A + TILE_B) / 16; e += P_NCONV * 32) {
+          uint4* src = e < TILE_A / 16 ? ah + e : bh + (e - TILE_A / 16);
+          uint4* dlo = e < TILE_A / 16 ? alo + e : blo + (e - TILE_A / 16);
+          uint4 v = *src;
+          uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+          uint4 l = make_uint4(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x)),
+                               __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y)),
+                               __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z)),
+                               __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w)));
+          *src = h;
+          *dlo = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[s]);
+      }
     }
   } else {
-    // converter warps 2..7: x -> hi (in place), lo = x - hi
-    const int cw = warp - CONV_WARP0;
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) break;
-      uint4* ah = (uint4*)A_hi(s);
-      uint4* bh = (uint4*)B_hi(s);
-      uint4* alo = (uint4*)A_lo(s);
-      uint4* blo = (uint4*)B_lo(s);
-      for (int e = cw * 32 + lane; e < (TILE_A + TILE_B) / 16; e += N_CONV_WARPS * 32) {
-        uint4* src = e < TILE_A / 16 ? ah + e : bh + (e - TILE_A / 16);
-        uint4* dlo = e < TILE_A / 16 ? alo + e : blo + (e - TILE_A / 16);
-        uint4 v = *src;
-        uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-        uint4 l = make_uint4(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x)),
-                             __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y)),
-                             __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z)),
-                             __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w)));
-        *src = h;
-        *dlo = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&conv[s]);
-    }
-  }
-
-  // epilogue: warps 4..7 drain TMEM lanes 32*(warp%4) ..
-  if (warp >= 4) {
-    const bool ok = mbar_wait(done, 0, abort_flag) && !*abort_flag;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const int q = warp % 4;
+    const int q = warp - P_EPI0;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int lc = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int64_t m0, n0;
+      tile_mn(tile, m0, n0);
+      int kb0, nk;
+      kslice(tile, kb0, nk);
+      const int nch = (nk + g.kch - 1) / g.kch;
       const int64_t m = m0 + q * 32 + lane;
       const bool mrow = m < g.M;
       const int64_t mo = mrow ? (m / g.om.mdiv) * g.om.c0 + (m % g.om.mdiv) * g.om.c1 : 0;
+      for (int ch = 0; ch < nch; ++ch, ++lc) {
+        const int buf = lc & 1;
+        if (!mbar_wait(&accf[buf], (lc >> 1) & 1, abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-      for (int cb = 0; cb < BN; cb += 32) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cb;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (mrow) {
+        for (int cb = 0; cb < BN; cb += 32) {
+          float c[32], hi[32], lo[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(buf * BN + cb), c);
+          if (ch == 0) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t n = n0 + cb + j;
-            if (n < g.N) g.C[mo + (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) * g.om.c3] = __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) { hi[j] = c[j]; lo[j] = 0.f; }
+          } else {
+            tmem_ld32(tmem + lane_base + (uint32_t)(2 * BN + cb), hi);
+            tmem_ld32(tmem + lane_base + (uint32_t)(3 * BN + cb), lo);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {   // two-sum: hi + c = s + e exactly
+              const float sm = hi[j] + c[j];
+              const float bp = sm - hi[j];
+              const float e = (hi[j] - (sm - bp)) + (c[j] - bp);
+              hi[j] = sm;
+              lo[j] += e;
+            }
+          }
+          if (ch + 1 < nch) {
+            tmem_st32(tmem + lane_base + (uint32_t)(2 * BN + cb), hi);
+            tmem_st32(tmem + lane_base + (uint32_t)(3 * BN + cb), lo);
+          } else if (mrow && !*abort_flag) {
+            if (g.nsplit > 1) {
+              float* prow = g.part + ((tile / (g.mt * g.nt)) * g.M + m) * g.N;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int64_t n = n0 + cb + j;
+                if (n < g.N) prow[n] = hi[j] + lo[j];
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int64_t n = n0 + cb + j;
+                if (n < g.N) g.C[mo + (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) * g.om.c3] = hi[j] + lo[j];
+              }
+            }
           }
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[buf]);
       }
     }
   }
 
-  // teardown: on abort, let the producer drain the loads it issued (bounded)
   if (warp == 0 && lane == 0 && *abort_flag) {
     for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it) {
       const int s = it % STAGES;
@@ -261,7 +382,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm_tf32x3(const __grid_consta
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * BN));
+  }
+}
+
+// Sum of the K-slice partials in FP64, written through the output map.
+__global__ void k_splitk_reduce(const float* __restrict__ part, int nsplit, int64_t M, int64_t N, OutMap om,
+                                float* __restrict__ C) {
+  const int64_t tot = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) acc += (double)part[sp * tot + e];
+    const int64_t m = e / N, n = e % N;
+    C[(m / om.mdiv) * om.c0 + (m % om.mdiv) * om.c1 + (n / om.ndiv) * om.c2 + (n % om.ndiv) * om.c3] = (float)acc;
   }
 }
 
@@ -305,7 +438,38 @@ bool gemm_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb
          M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31);
 }
 
-size_t gemm_tc_scratch_bytes(int, int64_t, int64_t, int64_t) { return 16; }
+constexpr int KCH_BLOCKS = 4;   // 128 terms per TMEM accumulation chunk
+
+// split over K only to fill the SMs when there are few output tiles
+static int nsplit_of(int64_t tiles, int64_t K, int sms) {
+  const int64_t nk = (K + BK - 1) / BK;
+  int best = 1;
+  double best_eff = 0;
+  for (int sp = 1; sp <= 8; ++sp) {
+    if ((int64_t)sp * KCH_BLOCKS > nk) break;
+    const int64_t t = tiles * sp;
+    const double eff = (double)t / (double)(((t + sms - 1) / sms) * sms);
+    if (eff > best_eff + 0.02) { best = sp; best_eff = eff; }
+    if (eff >= 0.9) break;
+  }
+  return best;
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    FP_CUDA(cudaGetDevice(&dev));
+    FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return sms;
+}
+
+size_t gemm_tc_scratch_bytes(int, int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int ns = nsplit_of(tiles, K, sm_count());
+  return 256 + (ns > 1 ? (size_t)ns * M * N * sizeof(float) : 0);
+}
 
 void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
              int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes) {
@@ -314,9 +478,10 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
   static bool attr = false;
   if (!attr) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_p, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr = true;
   }
+  const int sms = sm_count();
   CUtensorMap ma = make_map(A, M, K, lda, BM);
   CUtensorMap mb = make_map(B, N, K, ldb, BN);
   TcArgs g;
@@ -324,11 +489,27 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   g.mt = (M + BM - 1) / BM;
   g.nt = (N + BN - 1) / BN;
   g.m_fast = g.mt <= g.nt ? 1 : 0;
-  const int64_t blocks = g.mt * g.nt;
+  const int64_t nk = (K + BK - 1) / BK;
+  g.nsplit = nsplit_of(g.mt * g.nt, K, sms);
+  g.ks = (int)((nk + g.nsplit - 1) / g.nsplit);
+  g.nsplit = (int)((nk + g.ks - 1) / g.ks);   // every slice non-empty
+  g.kch = KCH_BLOCKS;
+  g.part = nullptr;
+  if (g.nsplit > 1) {
+    FP_CHECK(scratch_bytes >= gemm_tc_scratch_bytes(mode, M, N, K), FPEPS_ERR_ARG, "tensor-core GEMM: scratch too small");
+    g.part = (float*)((char*)scratch + 256);
+  }
+  const int64_t blocks = g.mt * g.nt * g.nsplit;
   FP_CHECK(blocks < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: grid too large");
   ProfToken pt = prof_begin(PROF_GEMM_TC, s, 2.0 * M * N * K, 4.0 * ((double)M * K + (double)N * K + (double)M * N));
-  k_gemm_tf32x3<<<(unsigned)blocks, NTHREADS, SMEM_BYTES, s>>>(ma, mb, g);
+  k_gemm_tf32x3_p<<<(unsigned)std::min<int64_t>(blocks, sms), P_THREADS, SMEM_BYTES, s>>>(ma, mb, g);
   FP_LAUNCH();
+  if (g.nsplit > 1) {
+    const int64_t tot = M * N;
+    const int rb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+    k_splitk_reduce<<<rb, 256, 0, s>>>(g.part, g.nsplit, M, N, om, C);
+    FP_LAUNCH();
+  }
   prof_end(pt, s);
 }
 

@@ -9,7 +9,10 @@
 // the sketched space in C order of its (bond, bundle) legs.
 //
 // One-sided Jacobi SVD: Hestenes' method with the cyclic round-robin ordering;
-// each rotation makes two columns orthogonal (Demmel and Veselic 1992).
+// each rotation makes two columns orthogonal (Demmel and Veselic 1992). The
+// path always applies it to the transposed triangular factor of a QR (the
+// preconditioned form of Drmac and Veselic 2008), where it converges in about
+// ten sweeps; the sweep count is capped at 30.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -711,7 +714,9 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
                     void* ws_dev) {
   FP_CHECK(k <= 1024, FPEPS_ERR_UNSUPPORTED, "svd: k > 1024");
   if (k <= 96) {
-    k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15, info);
+    // stopping rule |m_p.m_q| <= sqrt(k) eps |m_p||m_q|: a dot product of length k
+    // carries rounding of that size, so a fixed 1e-15 could never be met
+    k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15 * sqrt((double)k), info);
     FP_LAUNCH();
   } else {
     static int max_blocks = -1;
@@ -727,7 +732,7 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
     FP_CHECK(blocks >= 1, FPEPS_ERR_CUDA, "svd: no co-resident blocks");
     unsigned long long* ws = (unsigned long long*)ws_dev;
     int max_sweeps = 30;
-    double eps = 1e-15;
+    double eps = 1e-15 * sqrt((double)k);
     void* args[] = {&Mat, &V, &k, &max_sweeps, &eps, &ws};
     ProfToken pt = prof_begin(PROF_FACTOR, s, 0.0, 16.0 * k * k);
     count_launch();

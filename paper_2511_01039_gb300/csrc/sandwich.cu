@@ -129,8 +129,17 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
   for (int vw = 0; vw < o.nvw; ++vw) {
     for (int zw = 0; zw < o.nzw; ++zw) {
       const int pair = vw * o.nzw + zw;
-      for (int e = tid; e < nacc; e += blockDim.x) acc[e] = T(0);
       const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
+      if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
+        for (int e = tid; e < nv * nv * nz * nz; e += blockDim.x) {
+          int zp = e % nz, z = (e / nz) % nz, vp = (e / (nz * nz)) % nv, v = e / (nz * nz * nv);
+          int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp;
+          int64_t Z = ((int64_t)z * o.nzw + zw) * nz + zp;
+          O[V * o_V + Z * o_Z] = T(0);
+        }
+        continue;
+      }
+      for (int e = tid; e < nacc; e += blockDim.x) acc[e] = T(0);
       for (int c = c0; c < c1; ++c) {
         const int xw = o.d_ch[4 * c + 0], yw = o.d_ch[4 * c + 1];
         __syncthreads();
@@ -252,6 +261,17 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
     for (int zw = 0; zw < o.nzw; ++zw) {
       const int pair = vw * o.nzw + zw;
       const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
+      if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
+        for (int e = tid; e < M2 * N2; e += SM_THREADS) {
+          int m = e / N2, n = e % N2;
+          int bi = m / N2, vz = m % N2, v = vz / nz, z = vz % nz;
+          int vp = n / nz, zp = n % nz;
+          int64_t b = b0 + bi, t = b / nk, k = b % nk;
+          int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp, Z = ((int64_t)z * o.nzw + zw) * nz + zp;
+          out[t * o_t + k * o_k + V * o_V + Z * o_Z] = 0.f;
+        }
+        continue;
+      }
       float acc[3][6][4];
 #pragma unroll
       for (int i = 0; i < 3; ++i)

@@ -13,7 +13,7 @@ from oracle import boundary as B
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,tol", [("tf32x3", 2e-5), ("f32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("f32", 5e-5)])
 def test_central_site_theta_at_chi_500(prec, tol):
     import torch
     from paper_2511_01039_gb300 import fpeps as fp
@@ -35,5 +35,6 @@ def test_central_site_theta_at_chi_500(prec, tol):
     yo = B.theta(el.astype(np.float64), T.astype(np.float32).astype(np.float64), A.astype(np.float32).astype(np.float64),
                  W.astype(np.float32).astype(np.float64), np.moveaxis(x, 0, -1).astype(np.float64))
     yo = np.moveaxis(yo, -1, 0)
+    # inputs rounded to FP32 on both sides; the environment GEMM sums K = t * |L| = 108000 terms
     err = np.abs(y - yo).max() / np.abs(yo).max()
     assert err < tol, err
