@@ -204,6 +204,26 @@ fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const
  * and synchronises it. */
 fpeps_status fpeps_svd_f64(const double* M, int32_t k, double* U, double* sigma, double* V, void* cuda_stream);
 
+/* Largest k accepted by fpeps_svd_f64_noalloc. */
+#define FPEPS_SVD_NOALLOC_MAX_K 256
+
+/* Same SVD as fpeps_svd_f64, for callers that cannot allocate device memory
+ * during the call (for instance when another allocator already owns the whole
+ * device pool, or in a latency-critical loop where an allocation could stall or
+ * fail). It allocates nothing: its working storage (2 k^2 doubles, k ints and a
+ * few counters; about 1.05 MB) is a fixed device array inside the library, held
+ * on every GPU that loads the library until the process exits. The paper has no
+ * counterpart; this is an interface of this library only.
+ *   M (k x k, column-major, device, unchanged), U, V (k x k, column-major,
+ *   device), sigma (k, device): outputs as for fpeps_svd_f64.
+ *   1 <= k <= FPEPS_SVD_NOALLOC_MAX_K; larger k returns FPEPS_ERR_ARG.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race. Synchronises `cuda_stream`. */
+fpeps_status fpeps_svd_f64_noalloc(const double* M, int32_t k, double* U, double* sigma, double* V,
+                                   void* cuda_stream);
+
 /* Number of kernels this library has launched in the process so far. */
 int64_t fpeps_launch_count(void);
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "fpeps_gemm_f32": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.c_int64, C.c_void_p, C.c_void_p]),
     "fpeps_svd_f64": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fpeps_svd_f64_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fpeps_launch_count": (C.c_int64, []),
     "fpeps_profile": (C.c_int, [C.c_int32]),
     "fpeps_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -235,6 +236,19 @@ def fpeps_svd_f64(M, stream_handle: int = 0):
     V = torch.empty_like(Mc)
     s = torch.empty(k, dtype=torch.float64, device=M.device)
     _check(None, lib().fpeps_svd_f64(Mc.data_ptr(), k, U.data_ptr(), s.data_ptr(), V.data_ptr(), stream_handle))
+    return U.t(), s, V.t()
+
+
+def fpeps_svd_f64_noalloc(M, stream_handle: int = 0):
+    """fpeps_svd_f64 without device allocation in the library (k <= 256)."""
+    import torch
+    k = M.shape[0]
+    Mc = M.t().contiguous()
+    U = torch.empty_like(Mc)
+    V = torch.empty_like(Mc)
+    s = torch.empty(k, dtype=torch.float64, device=M.device)
+    _check(None, lib().fpeps_svd_f64_noalloc(Mc.data_ptr(), k, U.data_ptr(), s.data_ptr(), V.data_ptr(),
+                                             stream_handle))
     return U.t(), s, V.t()
 
 
