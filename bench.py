@@ -122,7 +122,6 @@ def cpu_sample(seconds: float, workload):
     EL = g.standard_normal((a, t, dL))
     nch = sum(1 for idx in np.ndindex(*W.shape[:4]) if np.any(W[idx] != 0))
     n_ld = len({(i[0], i[3]) for i in np.ndindex(*W.shape[:4]) if np.any(W[i] != 0)})
-    D6p = A.shape[0] ** 2 * A.shape[1] ** 2 * A.shape[2] * A.shape[3] * A.shape[4]
 
     def flops(k):   # same algorithmic count as the GPU path (structural PEPO zeros not counted)
         sand = 2.0 * t * k * A.shape[4] * (nch * (A.shape[1] * A.shape[2]) ** 2 * A.shape[0] * A.shape[3]
@@ -149,6 +148,21 @@ def cpu_sample(seconds: float, workload):
     desc = f"{done} Theta_c applications (column vectors) at site {c} of row {w.row}: chi={a}, t={t}, t'={tp}, " \
            f"bundles {dL}/{dR}/{dD}, numpy FP64"
     return tot_f / tot_t / 1e12, desc, cores
+
+
+# ----------------------------------------------------------------------------- ranks
+def reduce_ranks(dist, dev, seconds, work):
+    """Replicas exchange nothing on the data path; the timing is the slowest rank's
+    and the work is the sum over ranks. Returns (max seconds, summed work)."""
+    if dist is None:
+        return seconds, work
+    import torch
+    t = torch.tensor([seconds, work], dtype=torch.float64, device=dev)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item()
 
 
 # ----------------------------------------------------------------------------- main
@@ -233,14 +247,7 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = {fp.PROF_KINDS[k]: fp.fpeps_profile_read(k) for k in fp.PROF_KINDS}
     fp.fpeps_profile(False)
-    tot_flops = flops
-    if dist:
-        t = torch.tensor([ms, flops], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, tot_flops = mx[0].item(), sm[1].item()
+    ms, tot_flops = reduce_ranks(dist, dev, ms, flops)
     value = tot_flops / (ms * 1e-3) / 1e12
 
     # ---------------- end to end through host buffers
@@ -259,13 +266,7 @@ def main():
             ef += st.alg_flops
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el, ef], dtype=torch.float64, device=dev)
-            mx = t.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            sm = t.clone()
-            dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-            el, ef = mx[0].item(), sm[1].item()
+        el, ef = reduce_ranks(dist, dev, el, ef)
         e2e = {"value": ef / el / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": len(blob), "d2h_bytes_per_step": d2h,
                "seconds_per_step": el / args.steps}
 
@@ -280,13 +281,15 @@ def main():
     hbm = peaks.get("hbm_gbs", 6800.0)
     src = "of measured" if peaks else "of fallback"
     d = prof[dom]
-    if dom in ("gemm_tc_tf32x3",):
+    tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if args.prec == "tf32x3" else ("gemm_tc_tf32x3",)
+    if dom in tensor_kinds:
         # TF32 dense peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1/2.25)
         peak = bf16 * 1.1 / 2.25
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "note": f"algorithmic flops; 3xTF32 issues 3 MMAs per product so frac <= 1/3 ({src} BF16 x 1.1/2.25)"}
+                "note": f"TF32 peak = {src} BF16 x 1.1/2.25; algorithmic flops, and 3xTF32 issues 3 MMAs per "
+                        f"product, so frac <= 1/3"}
     elif dom in ("gemm_simt", "sandwich"):
         peak = 80.0
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0

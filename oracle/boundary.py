@@ -105,11 +105,50 @@ def form_theta(EL, T, A, W) -> np.ndarray:
 # linear algebra steps (Sec. IV; Halko et al. Example 1.6)
 # ---------------------------------------------------------------------------
 
+# A column whose squared residual, after projecting out the columns before it,
+# is at most DEP_TOL times the largest squared column norm is numerically
+# dependent on them (an FP64 Gram matrix cannot resolve it) and gives a zero column.
+DEP_TOL = 1e-13
+
+
 def orth(Y: np.ndarray) -> np.ndarray:
-    """Thin QR basis of the columns of Y, sign chosen so that diag(R) >= 0."""
-    Q, R = np.linalg.qr(Y)
-    s = np.where(np.diag(R) < 0, -1.0, 1.0)
-    return Q * s[None, :]
+    """Thin QR factor of Y (Sec. IV): columns orthonormalised in their order, so
+    that span(Q[:, :j]) = span(Y[:, :j]) and each column's coefficient on its own
+    direction is positive (diag(R) > 0, as LAPACK's QR with the sign fixed).
+
+    When Y is rank deficient, a column that depends numerically on the ones
+    before it (squared residual <= DEP_TOL * max squared column norm) becomes a
+    zero column instead of an arbitrary completion direction, so the non-zero
+    columns span exactly range(Y). Classical Gram-Schmidt, applied twice.
+    """
+    m, k = Y.shape
+    if m < k:
+        raise ValueError("orth: thin QR needs at least as many rows as columns")
+    Q = np.zeros((m, k))
+    if k == 0:
+        return Q
+    cap = DEP_TOL * float((Y * Y).sum(axis=0).max())
+    for j in range(k):
+        v = Y[:, j].astype(np.float64)
+        v = v - Q[:, :j] @ (Q[:, :j].T @ v)
+        r2 = float(v @ v)
+        if not r2 > cap:
+            continue
+        v = v - Q[:, :j] @ (Q[:, :j].T @ v)
+        Q[:, j] = v / np.sqrt(v @ v)
+    return Q
+
+
+# Singular vectors of a numerically zero singular value (sigma^2 <= NULL_TOL times
+# the sum of all sigma^2) are not determined by the matrix; they are taken as zero,
+# so that they add no bond direction.
+NULL_TOL = 1e-30
+
+
+def live(s: np.ndarray) -> np.ndarray:
+    """1.0 for singular values above the null level, 0.0 for the rest."""
+    tot = float((s * s).sum())
+    return ((s * s > NULL_TOL * tot) & (tot > 0)).astype(np.float64)
 
 
 def rsvd(apply, apply_t, omega: np.ndarray, q: int):
@@ -127,9 +166,19 @@ def rsvd(apply, apply_t, omega: np.ndarray, q: int):
     return Q, ub, s, vt
 
 
-def sign_of_sum(x: np.ndarray, axis: int) -> np.ndarray:
-    """+1 where the entry sum along ``axis`` is >= 0, else -1 (singular-vector gauge)."""
-    return np.where(x.sum(axis=axis) < 0, -1.0, 1.0)
+GAUGE_STAGE = 2   # sketch stage word of the gauge weights (0: zip-up, 1: CBE)
+
+
+def gauge_signs(x: np.ndarray, axis: int, *, seed: int, layer: int, site: int, row: int,
+                env: int = 0) -> np.ndarray:
+    """Sign gauge of kept singular vectors: +1 where sum_i w_i x_i >= 0 along ``axis``,
+    else -1, with fixed Gaussian weights w (the sketch generator, stage GAUGE_STAGE,
+    one column over the C-order flat index). A plain entry sum can vanish exactly
+    for symmetric vectors and leave the sign to rounding; generic weights cannot."""
+    w = gaussian_sketch(x.shape[axis], 1, seed=seed, layer=layer, stage=GAUGE_STAGE, site=site, row=row,
+                        env=env)[:, 0]
+    t = np.tensordot(w, x, axes=([0], [axis]))
+    return np.where(t < 0, -1.0, 1.0)
 
 
 # ---------------------------------------------------------------------------
@@ -179,8 +228,8 @@ def zipup(T, Arow, Wrow, chi: int, prm: RsvdParams, *, seed: int, layer: int, ro
             return theta_t(EL, T, A, W, Y.reshape(a, dDn, -1)).reshape(cols, -1)
 
         Q, ub, s, vt = rsvd(ap, ap_t, omega, prm.power_iters)
-        nc = Q @ ub[:, :chi_c]
-        sg = sign_of_sum(nc, 0)
+        nc = Q @ (ub[:, :chi_c] * live(s)[None, :chi_c])
+        sg = gauge_signs(nc, 0, seed=seed, layer=layer, site=c, row=row, env=env)
         nc = nc * sg[None, :]
         el = (sg * s[:chi_c])[:, None] * vt[:chi_c]
         nrm = np.linalg.norm(el)
@@ -221,7 +270,11 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
         A, W = Arow[c], Wrow[c]
         Al, Wl = Arow[c - 1], Wrow[c - 1]
         a_prev, dDn, a_c = M.shape
-        V = orth(M.reshape(a_prev, dDn * a_c).T).T                  # a_eff x (Dn a_c), orthonormal rows
+        if a_prev >= dDn * a_c:
+            # at least as many rows as columns: the row space is the whole (Dn a_c) space
+            V = np.eye(dDn * a_c)
+        else:
+            V = orth(M.reshape(a_prev, dDn * a_c).T).T              # a_prev x (Dn a_c), orthonormal rows
         a_eff = V.shape[0]
         Nl = N[c - 1]
         Nlm = Nl.reshape(-1, Nl.shape[2])                           # (a_{c-2} Dn_{c-1}) x a_{c-1}
@@ -251,7 +304,8 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
         if ct > 0:
             k = min(ct + prm.oversample, rows_a, cols_a)
             omega = gaussian_sketch(cols_a, k, seed=seed, layer=layer, stage=1, site=c, row=row, env=env)
-            _, _, _, vt = rsvd(a_apply, a_apply_t, omega, prm.power_iters)
+            _, _, sa, vt = rsvd(a_apply, a_apply_t, omega, prm.power_iters)
+            vt = vt * live(sa)[:, None]
             # the kept singular vectors lie in range(P_R^perp) unless A is (numerically)
             # rank deficient, when null-space vectors are arbitrary: a thin QR of
             # [V^T, Vtil^T] keeps V and makes the added rows orthogonal to it
@@ -261,9 +315,10 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
         ERp = theta_r(ER, T[c], A, W, Vp.T.reshape(dDn, a_c, -1))   # [t_{c-1}, L_c, j]
         Mp = theta(ELl, T[c - 1], Al, Wl, ERp)                      # [a_{c-2}, Dn_{c-1}, j]
         u, s, wt = np.linalg.svd(Mp.reshape(a2 * dDnl, -1), full_matrices=False)
+        wt = wt * live(s)[:, None]
         keep = min(chi, a2 * dDnl, Vp.shape[0])
         nc = wt[:keep] @ Vp
-        sg = sign_of_sum(nc, 1)
+        sg = gauge_signs(nc, 1, seed=seed, layer=layer, site=c, row=row, env=env)
         nc = nc * sg[:, None]
         out[c] = nc.reshape(keep, dDn, a_c)
         M = ((u[:, :keep] * s[:keep]) * sg[None, :]).reshape(a2, dDnl, keep)

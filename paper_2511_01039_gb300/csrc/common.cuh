@@ -116,7 +116,7 @@ void sandwich_apply(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk,
                     int64_t i_t, int64_t i_k, int64_t i_X, int64_t i_Y, T* out, int64_t o_t, int64_t o_k,
                     int64_t o_V, int64_t o_Z);
 
-// 3xTF32 tensor-core version (mma.sync), float data; needs D^2 <= 40, D^2 p <= 144.
+// 3xTF32 tensor-core version (mma.sync), float data; needs D <= 6 and D^2 p <= 144.
 bool sandwich_mma_fits(const SandOrient& o);
 void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const float* in, int64_t i_t,
                        int64_t i_k, int64_t i_X, int64_t i_Y, float* out, int64_t o_t, int64_t o_k, int64_t o_V,

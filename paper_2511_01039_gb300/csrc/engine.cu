@@ -26,10 +26,9 @@
 namespace fpeps {
 
 template <class T>
-void col_signs(cudaStream_t s, const T* X, int64_t m, int n, int64_t ld, double* sgn);
+void col_signs(cudaStream_t s, const T* X, int64_t m, int n, int64_t ld, const T* w, double* sgn);
 template <class T>
 void scale_cols(cudaStream_t s, T* X, int64_t m, int n, int64_t ld, const double* colscale);
-void svqb_factors(cudaStream_t s, const double* G, int k, double* work, double* Bt, double* Rq, int* info);
 void mul_vec(cudaStream_t s, const double* a, const double* b, double* out, int n);
 void gather_cols_f64(cudaStream_t s, const double* V, const int* order, int k, double* out);
 template <class T>
@@ -412,35 +411,24 @@ struct Engine : EngineBase {
   }
 
   // ---------------------------------------------------------------- QR (Sec. IV)
-  // Y (m x k, col-major, ld = m) = Q R. CholeskyQR2 in FP64 (Gram, Cholesky,
-  // Q = Y R^-1, twice); a pass whose Cholesky breaks down uses SVQB instead
-  // (eigenvectors of the scaled Gram, directions with eigenvalue below
-  // 1e-15 of the largest become zero columns). R: k x k row-major FP64, or null.
+  // Y (m x k, col-major, ld = m, m >= k) = Q R. CholeskyQR2 in FP64 (Gram,
+  // Cholesky, Q = Y R^-1, twice). Columns are orthonormalised in their order; a
+  // column whose Cholesky pivot (squared residual against the columns before it)
+  // is at most 1e-13 of the largest squared column norm depends numerically on
+  // them and gives a zero column of Q and a zero row of R. R: k x k row-major
+  // FP64, or null.
   void one_pass(Arena& ar, const T* Y, int64_t m, int k, T* Q, double* R) {
     double* G = ar.get_n<double>((int64_t)k * k);
     gram_f64<T>(s, Y, m, k, m, G);
     cholesky_upper_f64(s, G, k, env->d_info, ar.get_n<double>(8));
+    FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "QR: non-finite Gram matrix");
     T* Bt = ar.get_n<T>((int64_t)k * k);
-    if (read_info() == 0) {
-      double* Rinv = ar.get_n<double>((int64_t)k * k);
-      tri_inverse_upper_f64(s, G, k, Rinv);
-      convert_f64<T>(s, Rinv, Bt, (int64_t)k * k);
-      // Q(m, j) = sum_i Y(m, i) Rinv(i, j);  Rinv row-major
-      gemm_simt<T>(s, m, k, k, T(1), Y, 1, m, Bt, 1, k, T(0), Q, out_colmajor(m, k, m));
-      if (R) FP_CUDA(cudaMemcpyAsync(R, G, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
-      return;
-    }
-    // SVQB
-    gram_f64<T>(s, Y, m, k, m, G);
-    double* work = ar.get_n<double>((int64_t)6 * k * k + 4 * k + 64);
-    double* Bt64 = ar.get_n<double>((int64_t)k * k);
-    double* Rq = ar.get_n<double>((int64_t)k * k);
-    svqb_factors(s, G, k, work, Bt64, Rq, env->d_info);
-    FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "QR: eigen-decomposition did not converge");
-    convert_f64<T>(s, Bt64, Bt, (int64_t)k * k);
-    // Q(m, j) = sum_i Y(m, i) Bt(i, j), Bt col-major
-    gemm_simt<T>(s, m, k, k, T(1), Y, 1, m, Bt, k, 1, T(0), Q, out_colmajor(m, k, m));
-    if (R) FP_CUDA(cudaMemcpyAsync(R, Rq, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
+    double* Rinv = ar.get_n<double>((int64_t)k * k);
+    tri_inverse_upper_f64(s, G, k, Rinv);
+    convert_f64<T>(s, Rinv, Bt, (int64_t)k * k);
+    // Q(m, j) = sum_i Y(m, i) Rinv(i, j);  Rinv row-major
+    gemm_simt<T>(s, m, k, k, T(1), Y, 1, m, Bt, 1, k, T(0), Q, out_colmajor(m, k, m));
+    if (R) FP_CUDA(cudaMemcpyAsync(R, G, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
   }
 
   void qr(const T* Y, int64_t m, int k, T* Q, double* R) {
@@ -632,8 +620,13 @@ struct Engine : EngineBase {
       convert_f64<T>(s, r.U, Ut, (int64_t)k * k);
       T* N = rowmem.get_n<T>(rows * chi_c);
       mm(rows, chi_c, k, T(1), r.Q, false, rows, Ut, false, k, T(0), N, rows);
+      // sign gauge: weights from the sketch generator (stage 2) over the (a, Dn)
+      // flat index; rows are stored Dn-major with a fastest
       double* sgn = ar.get_n<double>(chi_c);
-      col_signs<T>(s, N, rows, chi_c, rows, sgn);
+      T* gw = ar.get_n<T>(rows);
+      int64_t gperm[2] = {st.bD, a};
+      gaussian_sketch<T>(s, gw, rows, 1, rows, gperm, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16), w3);
+      col_signs<T>(s, N, rows, chi_c, rows, gw, sgn);
       scale_cols<T>(s, N, rows, chi_c, rows, sgn);
       // EL_{c+1} vectors = Q_b W[:, :chi] diag(sigma * sign)
       double* sc = ar.get_n<double>(chi_c);
@@ -808,6 +801,15 @@ struct Engine : EngineBase {
                 mm(cols_a, kk, a_eff, T(-1), VT, false, cols_a, tmpA, false, a_eff, T(1), X, cols_a);
               }};
         RsvdOut r = rsvd(ar, A, omega, k, prm.power_iters);
+        // right singular vectors of numerically zero singular values are not
+        // determined by A: zero columns (sigma is sorted, so they are the last)
+        {
+          double tot = 0;
+          for (double sv : r.sigma) tot += sv * sv;
+          int live = 0;
+          while (live < ct && r.sigma[live] * r.sigma[live] > 1e-30 * tot) ++live;
+          if (live < ct) FP_CUDA(cudaMemsetAsync(r.QbW + cols_a * live, 0, sizeof(T) * cols_a * (ct - live), s));
+        }
         // V' = orth([V^T | Vtil^T])
         j = a_eff + ct;
         T* cat = ar.get_n<T>(cols_a * j);
@@ -849,7 +851,10 @@ struct Engine : EngineBase {
       T* Nc = (T*)e->al.get(sizeof(T) * cols_a * keep);
       mm(cols_a, keep, j, T(1), Vp, false, cols_a, Wt, false, j, T(0), Nc, cols_a);
       double* sgn = ar.get_n<double>(keep);
-      col_signs<T>(s, Nc, cols_a, keep, cols_a, sgn);
+      T* gw = ar.get_n<T>(cols_a);
+      gaussian_sketch<T>(s, gw, cols_a, 1, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16),
+                         w3);
+      col_signs<T>(s, Nc, cols_a, keep, cols_a, gw, sgn);
       scale_cols<T>(s, Nc, cols_a, keep, cols_a, sgn);
       T_new[c] = Nc;
       tb_new[c] = keep;

@@ -17,7 +17,7 @@
 //
 // Accumulation: the tensor cores' FP32 accumulation over long K loses far more
 // than round-to-nearest FP32 (measured ~1e-5 relative at K = 2048, ~1e-3 at
-// K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 128 terms; each
+// K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 256 terms; each
 // chunk accumulates in a fresh TMEM buffer (two buffers, so the MMAs of chunk
 // i+1 overlap the drain of chunk i) and the epilogue warps fold it into a
 // compensated running sum (hi, lo) kept in the other half of TMEM (Knuth's
@@ -121,6 +121,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+// issue without waiting; tmem_wait32 then waits for every load in flight and
+// ties the registers of one batch to that wait
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait32(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
 }
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
   asm volatile(
@@ -325,13 +347,24 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
 #pragma unroll 1
         for (int cb = 0; cb < BN; cb += 32) {
           float c[32], hi[32], lo[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(buf * BN + cb), c);
+          uint32_t rc[32], rh[32], rl[32];
+          tmem_ld32_async(tmem + lane_base + (uint32_t)(buf * BN + cb), rc);
           if (ch == 0) {
+            tmem_wait32(rc);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) { hi[j] = c[j]; lo[j] = 0.f; }
+            for (int j = 0; j < 32; ++j) { c[j] = __uint_as_float(rc[j]); hi[j] = c[j]; lo[j] = 0.f; }
           } else {
-            tmem_ld32(tmem + lane_base + (uint32_t)(2 * BN + cb), hi);
-            tmem_ld32(tmem + lane_base + (uint32_t)(3 * BN + cb), lo);
+            tmem_ld32_async(tmem + lane_base + (uint32_t)(2 * BN + cb), rh);
+            tmem_ld32_async(tmem + lane_base + (uint32_t)(3 * BN + cb), rl);
+            tmem_wait32(rc);
+            tmem_wait32(rh);
+            tmem_wait32(rl);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              c[j] = __uint_as_float(rc[j]);
+              hi[j] = __uint_as_float(rh[j]);
+              lo[j] = __uint_as_float(rl[j]);
+            }
 #pragma unroll
             for (int j = 0; j < 32; ++j) {   // two-sum: hi + c = s + e exactly
               const float sm = hi[j] + c[j];
@@ -438,7 +471,7 @@ bool gemm_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb
          M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31);
 }
 
-constexpr int KCH_BLOCKS = 4;   // 128 terms per TMEM accumulation chunk
+constexpr int KCH_BLOCKS = 8;   // 256 terms per TMEM accumulation chunk (K <= 512: one chunk)
 
 // split over K only to fill the SMs when there are few output tiles
 static int nsplit_of(int64_t tiles, int64_t K, int sms) {
@@ -493,7 +526,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   g.nsplit = nsplit_of(g.mt * g.nt, K, sms);
   g.ks = (int)((nk + g.nsplit - 1) / g.nsplit);
   g.nsplit = (int)((nk + g.ks - 1) / g.ks);   // every slice non-empty
-  g.kch = KCH_BLOCKS;
+  g.kch = g.ks <= 2 * KCH_BLOCKS ? g.ks : KCH_BLOCKS;
   g.part = nullptr;
   if (g.nsplit > 1) {
     FP_CHECK(scratch_bytes >= gemm_tc_scratch_bytes(mode, M, N, K), FPEPS_ERR_ARG, "tensor-core GEMM: scratch too small");

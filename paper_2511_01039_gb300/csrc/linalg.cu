@@ -166,8 +166,10 @@ __global__ void k_mirror_upper(double* G, int k) {
   }
 }
 
-// In-place Cholesky G = R^T R (R upper, row-major), one block. info = 1 when a
-// pivot is not positive or falls below tol * max diag (numerical rank loss).
+// In-place Cholesky G = R^T R (R upper, row-major), one block, for the Gram
+// matrix of the columns of Y. A pivot at or below tol * max diag means column j
+// depends numerically on the columns before it: row j of R is set to zero (the
+// column of Q it would give is zero). info = 1 only for non-finite input.
 __global__ void __launch_bounds__(1024) k_cholesky(double* G, int k, double tol, int* info) {
   __shared__ double piv_s;
   __shared__ double dmax_s;
@@ -175,23 +177,28 @@ __global__ void __launch_bounds__(1024) k_cholesky(double* G, int k, double tol,
   const int tid = threadIdx.x;
   if (tid == 0) {
     double dm = 0;
-    for (int i = 0; i < k; ++i) dm = fmax(dm, G[(int64_t)i * k + i]);
+    bool fin = true;
+    for (int i = 0; i < k; ++i) {
+      const double d = G[(int64_t)i * k + i];
+      fin = fin && isfinite(d);
+      dm = fmax(dm, d);
+    }
     dmax_s = dm;
-    bad = !(dm > 0) || !isfinite(dm);
+    bad = !fin;
   }
   __syncthreads();
   if (bad) { if (tid == 0) info[0] = 1; return; }
   for (int j = 0; j < k; ++j) {
     if (tid == 0) {
-      double d = G[(int64_t)j * k + j];
-      if (!(d > tol * dmax_s) || !isfinite(d)) bad = 1;
-      piv_s = sqrt(fmax(d, 0.0));
+      const double d = G[(int64_t)j * k + j];
+      if (!isfinite(d)) bad = 1;
+      piv_s = d > tol * dmax_s ? sqrt(d) : 0.0;
       G[(int64_t)j * k + j] = piv_s;
     }
     __syncthreads();
     if (bad) { if (tid == 0) info[0] = 1; return; }
     const double piv = piv_s;
-    for (int c = j + 1 + tid; c < k; c += blockDim.x) G[(int64_t)j * k + c] /= piv;
+    for (int c = j + 1 + tid; c < k; c += blockDim.x) G[(int64_t)j * k + c] = piv > 0 ? G[(int64_t)j * k + c] / piv : 0.0;
     __syncthreads();
     const int n = k - j - 1;
     // trailing update of the upper triangle: G[i][c] -= R[j][i] R[j][c], i <= c
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(1024) k_cholesky(double* G, int k, double tol,
 // Blocked right-looking Cholesky over the whole GPU (cooperative launch, panel
 // width 32): block 0 factors the diagonal block in shared memory, every block
 // solves its share of the panel row, every block updates its share of the
-// trailing upper triangle; grid barriers in between. Same pivot test as above.
+// trailing upper triangle; grid barriers in between. Same pivot rule as above.
 constexpr int CH_NB = 32;
 __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double tol, int* info, double* ws) {
   namespace cg = cooperative_groups;
@@ -223,9 +230,14 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
   const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && tid == 0) {
     double dm = 0;
-    for (int i = 0; i < k; ++i) dm = fmax(dm, G[(int64_t)i * k + i]);
+    bool fin = true;
+    for (int i = 0; i < k; ++i) {
+      const double d = G[(int64_t)i * k + i];
+      fin = fin && isfinite(d);
+      dm = fmax(dm, d);
+    }
     ws[0] = dm;
-    info[0] = !(dm > 0) || !isfinite(dm);
+    info[0] = !fin;
   }
   grid.sync();
   if (*(volatile int*)info) return;
@@ -238,13 +250,13 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
       __syncthreads();
       for (int j = 0; j < nb; ++j) {
         if (tid == 0) {
-          double d = D[j][j];
-          if (!(d > tol * dmax) || !isfinite(d)) bad_s = 1;
-          D[j][j] = sqrt(fmax(d, 0.0));
+          const double d = D[j][j];
+          if (!isfinite(d)) bad_s = 1;
+          D[j][j] = d > tol * dmax ? sqrt(d) : 0.0;
         }
         __syncthreads();
         if (bad_s) break;
-        for (int c = j + 1 + tid; c < nb; c += blockDim.x) D[j][c] /= D[j][j];
+        for (int c = j + 1 + tid; c < nb; c += blockDim.x) D[j][c] = D[j][j] > 0 ? D[j][c] / D[j][j] : 0.0;
         __syncthreads();
         const int n = nb - j - 1;
         for (int e = tid; e < n * n; e += blockDim.x) {
@@ -266,7 +278,8 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
       for (int i = 0; i < nb; ++i) {
         double x = G[(int64_t)(p0 + i) * k + c];
         for (int l = 0; l < i; ++l) x -= G[(int64_t)(p0 + l) * k + p0 + i] * G[(int64_t)(p0 + l) * k + c];
-        G[(int64_t)(p0 + i) * k + c] = x / G[(int64_t)(p0 + i) * k + p0 + i];
+        const double piv = G[(int64_t)(p0 + i) * k + p0 + i];
+        G[(int64_t)(p0 + i) * k + c] = piv > 0 ? x / piv : 0.0;
       }
     }
     grid.sync();
@@ -289,7 +302,8 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
 
 // Rinv = R^{-1} for upper-triangular R (row-major): one warp per column, the
 // back-substitution dot products split over the lanes, the column kept in
-// shared memory.
+// shared memory. Rows of R with a zero diagonal (dependent columns) give zero
+// rows and columns of Rinv: the inverse of the non-zero part, padded with zeros.
 __global__ void __launch_bounds__(128) k_tri_inverse_warp(const double* R, int k, double* Rinv) {
   extern __shared__ double xs_all[];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
@@ -298,32 +312,22 @@ __global__ void __launch_bounds__(128) k_tri_inverse_warp(const double* R, int k
   if (j >= k) return;
   for (int i = lane; i < k; i += 32) x[i] = 0.0;
   __syncwarp();
-  if (lane == 0) x[j] = 1.0 / R[(int64_t)j * k + j];
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    double sdot = 0;
-    for (int l = i + 1 + lane; l <= j; l += 32) sdot = fma(R[(int64_t)i * k + l], x[l], sdot);
-    for (int o = 16; o; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
-    if (lane == 0) x[i] = -sdot / R[(int64_t)i * k + i];
+  const double rjj = R[(int64_t)j * k + j];
+  if (rjj != 0.0) {
+    if (lane == 0) x[j] = 1.0 / rjj;
     __syncwarp();
-  }
-  for (int i = lane; i < k; i += 32) Rinv[(int64_t)i * k + j] = x[i];
-}
-
-// Rinv = R^{-1} for upper-triangular R (row-major); column j solved by thread j.
-__global__ void k_tri_inverse(const double* R, int k, double* Rinv) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
-    for (int i = k - 1; i >= 0; --i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      if (i <= j) {
-        for (int l = i + 1; l <= j; ++l) s -= R[(int64_t)i * k + l] * Rinv[(int64_t)l * k + j];
-        s /= R[(int64_t)i * k + i];
-      } else {
-        s = 0.0;
-      }
-      Rinv[(int64_t)i * k + j] = s;
+    for (int i = j - 1; i >= 0; --i) {
+      const double rii = R[(int64_t)i * k + i];
+      if (rii == 0.0) continue;   // x[i] stays zero
+      double sdot = 0;
+      for (int l = i + 1 + lane; l <= j; l += 32) sdot = fma(R[(int64_t)i * k + l], x[l], sdot);
+      for (int o = 16; o; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+      if (lane == 0) x[i] = -sdot / rii;
+      __syncwarp();
     }
   }
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) Rinv[(int64_t)i * k + j] = x[i];
 }
 
 // One round of the one-sided Jacobi method on the columns of M (col-major,
@@ -551,12 +555,13 @@ __global__ void k_finite(const T* x, int64_t n, int* flag) {
 
 
 // ---- small helpers used by the engine -------------------------------------
-// s_j = +1 if sum_i X(i, j) >= 0 else -1 (singular-vector sign gauge); one block per column
+// s_j = +1 if sum_i w_i X(i, j) >= 0 else -1 (singular-vector sign gauge with
+// fixed Gaussian weights w); one block per column
 template <class T>
-__global__ void k_col_signs(const T* X, int64_t m, int64_t ld, double* sgn) {
+__global__ void k_col_signs(const T* X, int64_t m, int64_t ld, const T* w, double* sgn) {
   const int j = blockIdx.x;
   double s = 0;
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += (double)X[(int64_t)j * ld + i];
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s = fma((double)w[i], (double)X[(int64_t)j * ld + i], s);
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   __shared__ double ws[32];
   if (threadIdx.x % 32 == 0) ws[threadIdx.x / 32] = s;
@@ -592,33 +597,6 @@ template <class T>
 __global__ void k_set_identity(T* X, int64_t m, int n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * n; e += (int64_t)gridDim.x * blockDim.x)
     X[e] = (e / m == e % m) ? T(1) : T(0);
-}
-
-// SVQB factors from the Gram matrix G (k x k): d_i = G_ii^{-1/2}, scaled Gram
-// D G D = V diag(lam) V^T (one-sided Jacobi of a symmetric PSD matrix gives its
-// eigenvectors as right singular vectors), kept where lam_r > 1e-15 lam_0.
-//   Bt (col-major)  = D V diag(lam^{-1/2})        Y Bt = Q
-//   Rq (row-major)  = diag(lam^{1/2}) V^T D^{-1}  Y ~= Q Rq
-__global__ void k_svqb_scale(const double* G, int k, double* d, double* Gs) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / k), j = (int)(e % k);
-    double gi = G[(int64_t)i * k + i], gj = G[(int64_t)j * k + j];
-    double di = gi > 0 ? rsqrt(gi) : 0.0, dj = gj > 0 ? rsqrt(gj) : 0.0;
-    Gs[e] = G[e] * di * dj;
-    if (j == 0) d[i] = di;
-  }
-}
-
-__global__ void k_svqb_factors(const double* V, const double* lam, const double* d, int k, double* Bt, double* Rq) {
-  const double lmax = lam[0];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e / k), i = (int)(e % k);   // column r, row i
-    double l = lam[r];
-    bool keep = l > 1e-15 * lmax && lmax > 0;
-    double v = V[(int64_t)r * k + i];
-    Bt[(int64_t)r * k + i] = keep ? d[i] * v / sqrt(l) : 0.0;
-    Rq[(int64_t)r * k + i] = (keep && d[i] > 0) ? sqrt(l) * v / d[i] : 0.0;
-  }
 }
 
 int grid_for(int64_t n) {
@@ -792,9 +770,9 @@ void check_finite(cudaStream_t s, const T* x, int64_t n, int* flag) {
 
 
 template <class T>
-void col_signs(cudaStream_t s, const T* X, int64_t m, int n, int64_t ld, double* sgn) {
+void col_signs(cudaStream_t s, const T* X, int64_t m, int n, int64_t ld, const T* w, double* sgn) {
   if (n <= 0) return;
-  k_col_signs<T><<<n, 256, 0, s>>>(X, m, ld, sgn);
+  k_col_signs<T><<<n, 256, 0, s>>>(X, m, ld, w, sgn);
   FP_LAUNCH();
 }
 template <class T>
@@ -820,22 +798,6 @@ template <class T>
 void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst) {
   FP_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, s));
 }
-void svqb_factors(cudaStream_t s, const double* G, int k, double* work, double* Bt, double* Rq, int* info) {
-  double* d = work;
-  double* Gs = d + k;
-  double* U = Gs + (int64_t)k * k;
-  double* V = U + (int64_t)k * k;
-  double* Vs = V + (int64_t)k * k;
-  double* lam = Vs + (int64_t)k * k;
-  int* order = (int*)(lam + k);
-  void* jws = (void*)(((uintptr_t)(order + k) + 63) & ~(uintptr_t)63);
-  k_svqb_scale<<<grid_for((int64_t)k * k), 256, 0, s>>>(G, k, d, Gs);
-  FP_LAUNCH();
-  svd_jacobi_f64(s, Gs, k, U, lam, V, order, info, jws);
-  gather_cols_f64(s, V, order, k, Vs);
-  k_svqb_factors<<<grid_for((int64_t)k * k), 256, 0, s>>>(Vs, lam, d, k, Bt, Rq);
-  FP_LAUNCH();
-}
 
 #define INST(T)                                                                                              \
   template void gaussian_sketch<T>(cudaStream_t, T*, int64_t, int64_t, int64_t, const int64_t*, uint64_t,    \
@@ -848,7 +810,7 @@ void svqb_factors(cudaStream_t s, const double* G, int k, double* work, double* 
   template void permute3<T>(cudaStream_t, const T*, T*, int64_t, int64_t, int64_t, int, int, int);            \
   template void fill<T>(cudaStream_t, T*, int64_t, T);                                                        \
   template void check_finite<T>(cudaStream_t, const T*, int64_t, int*);                                      \
-  template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, double*);                         \
+  template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, const T*, double*);                         \
   template void scale_cols<T>(cudaStream_t, T*, int64_t, int, int64_t, const double*);                        \
   template void set_identity<T>(cudaStream_t, T*, int64_t, int);                                              \
   template void copy_cols<T>(cudaStream_t, const T*, int64_t, int, T*);

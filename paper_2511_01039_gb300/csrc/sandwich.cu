@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
 // nearest) and the three products hi*hi + hi*lo + lo*hi accumulate in FP32.
 constexpr int SM_MT = 9, SM_PA = 44, SM_PB = 152, SM_PC = 148, SM_PR = 40;
 constexpr int SM_THREADS = 288;   // 9 warps
-constexpr int SM_FLOATS = 144 * SM_PA + 40 * SM_PB + 144 * SM_PC + 144 * SM_PR;
+constexpr int SM_FLOATS = 2 * 144 * SM_PA + 2 * 40 * SM_PB + 144 * SM_PC + 144 * SM_PR + 2 * (2 * 144 + 4 * 36) + 36;
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -225,30 +225,68 @@ __device__ __forceinline__ void mma3(float* d, const float* af, const float* bf)
   mma_tf32_16x8x8(d, ah, bh);
 }
 
+// Offsets are tabulated once per CTA (block bases, bundle rows and columns;
+// the PEPO channel only shifts them by a constant), the gathers of a channel
+// are issued as cp.async copies into one of two A/B buffers while the MMAs of
+// the previous channel run, and the output tile is staged so that it is
+// written in contiguous runs.
+constexpr int SM_GROUPS = 8;   // groups of nb_per blocks handled by one CTA
+constexpr int SM_TILE_FLOATS = 2 * 144 * SM_PA + 2 * 40 * SM_PB + 144 * SM_PC + 144 * SM_PR;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, int64_t nt, int64_t nk, int nb_per,
                                                                 const float* __restrict__ in, int64_t i_t,
                                                                 int64_t i_k, int64_t i_X, int64_t i_Y,
                                                                 float* __restrict__ out, int64_t o_t, int64_t o_k,
                                                                 int64_t o_V, int64_t o_Z) {
   extern __shared__ float sm[];
-  float* sA = sm;                       // [144][SM_PA]   rows (b, x', y'), cols (x, y)
-  float* sB = sA + 144 * SM_PA;         // [40][SM_PB]    rows (x, y), cols (v, z, q)
-  float* sC = sB + 40 * SM_PB;          // [144][SM_PC]   rows (b, v, z), cols (x', y', q)
-  float* sR = sC + 144 * SM_PC;         // [144][SM_PR]   rows (x', y', q), cols (v', z')
+  float* sAb[2] = {sm, sm + 144 * SM_PA};                       // [144][SM_PA] rows (b, x', y'), cols (x, y)
+  float* sBb[2] = {sm + 2 * 144 * SM_PA, sm + 2 * 144 * SM_PA + 40 * SM_PB};   // [40][SM_PB] (x,y) x (v,z,q)
+  float* sC = sm + 2 * 144 * SM_PA + 2 * 40 * SM_PB;            // [144][SM_PC] rows (b, v, z), cols (x', y', q)
+  float* sR = sC + 144 * SM_PC;                                 // [144][SM_PR] rows (x', y', q), cols (v', z')
+  int64_t* bin = reinterpret_cast<int64_t*>(sR + 144 * SM_PR);  // [144] block input bases
+  int64_t* bout = bin + 144;                                    // [144] block output bases
+  int64_t* rowX0 = bout + 144;                                  // [36] (x, x') at channel x_w = 0
+  int64_t* colY0 = rowX0 + 36;                                  // [36] (y, y') at y_w = 0
+  int64_t* offV0 = colY0 + 36;                                  // [36] (v, v') at v_w = 0
+  int64_t* offZ0 = offV0 + 36;                                  // [36] (z, z') at z_w = 0
+  int* dyy = reinterpret_cast<int*>(offZ0 + 36);                // [36] A-tile offset of (y, y')
   const float* AW = static_cast<const float*>(o.d_aw);
   const float* AR = static_cast<const float*>(o.d_ar);
   const int nx = o.nx, ny = o.ny, nv = o.nv, nz = o.nz, p = o.p;
   const int K1 = nx * ny, N1 = nv * nz * p, K2 = nx * ny * p, N2 = nv * nz;
-  const int K1p = (K1 + 7) & ~7;
+  const int K1p = (K1 + 7) & ~7, K2p = (K2 + 7) & ~7;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int g = lane >> 2, q4 = lane & 3;
+  const int mg = warp / 3, ng = warp % 3;
   const int64_t nblk = nt * nk;
-  const int64_t b0 = (int64_t)blockIdx.x * nb_per;
-  const int nb = (int)min((int64_t)nb_per, nblk - b0);
-  const int M1 = nb * K1, M2 = nb * N2;
+  const bool v_contig = (o_V == 1);
+  const bool aw16 = (N1 % 4) == 0 && ((uintptr_t)AW % 16) == 0;
 
-  // zero everything once (padding must read as zero), then the bra operand
-  for (int e = tid; e < SM_FLOATS; e += SM_THREADS) sm[e] = 0.f;
+  for (int e = tid; e < SM_TILE_FLOATS; e += SM_THREADS) sm[e] = 0.f;
+  if (tid < 36) {
+    if (tid < nx * nx) rowX0[tid] = ((int64_t)(tid / nx) * o.nxw * nx + tid % nx) * i_X;
+    if (tid < ny * ny) {
+      colY0[tid] = ((int64_t)(tid / ny) * o.nyw * ny + tid % ny) * i_Y;
+      dyy[tid] = (tid % ny) * SM_PA + tid / ny;
+    }
+    if (tid < nv * nv) offV0[tid] = ((int64_t)(tid / nv) * o.nvw * nv + tid % nv) * o_V;
+    if (tid < nz * nz) offZ0[tid] = ((int64_t)(tid / nz) * o.nzw * nz + tid % nz) * o_Z;
+  }
   __syncthreads();
   for (int e = tid; e < K2 * N2; e += SM_THREADS) {
     int r = e / N2, c = e % N2;            // r = (x', y', q), c = (v', z')
@@ -257,119 +295,172 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
     sR[r * SM_PR + c] = AR[(((xp * ny + yp) * nv + vp) * nz + zp) * p + q];
   }
 
-  for (int vw = 0; vw < o.nvw; ++vw) {
-    for (int zw = 0; zw < o.nzw; ++zw) {
-      const int pair = vw * o.nzw + zw;
-      const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
-      if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
-        for (int e = tid; e < M2 * N2; e += SM_THREADS) {
-          int m = e / N2, n = e % N2;
-          int bi = m / N2, vz = m % N2, v = vz / nz, z = vz % nz;
-          int vp = n / nz, zp = n % nz;
-          int64_t b = b0 + bi, t = b / nk, k = b % nk;
-          int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp, Z = ((int64_t)z * o.nzw + zw) * nz + zp;
-          out[t * o_t + k * o_k + V * o_V + Z * o_Z] = 0.f;
-        }
-        continue;
+  for (int grp = 0; grp < SM_GROUPS; ++grp) {
+    const int64_t b0 = ((int64_t)blockIdx.x * SM_GROUPS + grp) * nb_per;
+    if (b0 >= nblk) break;
+    const int nb = (int)min((int64_t)nb_per, nblk - b0);
+    const int M1 = nb * K1, M2 = nb * N2;
+    __syncthreads();   // previous group done with every table and tile
+    for (int bi = tid; bi < nb; bi += SM_THREADS) {
+      const int64_t b = b0 + bi, t = b / nk, k = b % nk;
+      bin[bi] = t * i_t + k * i_k;
+      bout[bi] = t * o_t + k * o_k;
+    }
+    __syncthreads();
+
+    // gathers of channel c into buffer buf (cp.async)
+    auto issue = [&](int c, int buf) {
+      const int xw = o.d_ch[4 * c + 0], yw = o.d_ch[4 * c + 1];
+      const int64_t dx = (int64_t)xw * nx * i_X, dy = (int64_t)yw * ny * i_Y;
+      float* A = sAb[buf];
+      for (int r = warp; r < nb * nx * nx; r += SM_THREADS / 32) {
+        const int bi = r / (nx * nx), xx = r % (nx * nx), x = xx / nx, xp = xx % nx;
+        const float* src = in + bin[bi] + rowX0[xx] + dx + dy;
+        float* dst = A + (bi * K1 + xp * ny) * SM_PA + x * ny;
+        for (int yy = lane; yy < ny * ny; yy += 32) cp_async4(dst + dyy[yy], src + colY0[yy]);
       }
-      float acc[3][6][4];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-      const int mg = warp / 3, ng = warp % 3;
-      for (int c = c0; c < c1; ++c) {
-        const int xw = o.d_ch[4 * c + 0], yw = o.d_ch[4 * c + 1];
-        __syncthreads();
-        // A: rows (bi, x', y'), cols (x, y) from block bi's input
-        for (int e = tid; e < M1 * K1; e += SM_THREADS) {
-          int m = e / K1, kk = e % K1;
-          int bi = m / K1, xy = m % K1, xp = xy / ny, yp = xy % ny;
-          int x = kk / ny, y = kk % ny;
-          int64_t b = b0 + bi, t = b / nk, k = b % nk;
-          int64_t X = ((int64_t)x * o.nxw + xw) * nx + xp, Y = ((int64_t)y * o.nyw + yw) * ny + yp;
-          sA[m * SM_PA + kk] = in[t * i_t + k * i_k + X * i_X + Y * i_Y];
+      const float* awc = AW + (int64_t)c * K1 * N1;
+      float* Bm = sBb[buf];
+      if (aw16) {
+        const int n4 = N1 / 4;
+        for (int e = tid; e < K1 * n4; e += SM_THREADS) {
+          const int r = e / n4, c4 = e % n4;
+          cp_async16(Bm + r * SM_PB + 4 * c4, awc + (int64_t)r * N1 + 4 * c4);
         }
-        const float* awc = AW + (int64_t)c * K1 * N1;
-        for (int e = tid; e < K1 * N1; e += SM_THREADS) sB[(e / N1) * SM_PB + e % N1] = awc[e];
-        __syncthreads();
-        for (int k0 = 0; k0 < K1p; k0 += 8) {
-          float af[3][4], bf[6][2];
+      } else {
+        for (int r = warp; r < K1; r += SM_THREADS / 32)
+          for (int n = lane; n < N1; n += 32) cp_async4(Bm + r * SM_PB + n, awc + (int64_t)r * N1 + n);
+      }
+    };
+
+    for (int vw = 0; vw < o.nvw; ++vw) {
+      for (int zw = 0; zw < o.nzw; ++zw) {
+        const int pair = vw * o.nzw + zw;
+        const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
+        const int64_t dv = (int64_t)vw * nv * o_V, dz = (int64_t)zw * nz * o_Z;
+        if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
+          const int ninner = v_contig ? nv * nv : nz * nz, nouter = v_contig ? nz * nz : nv * nv;
+          for (int r = warp; r < nb * nouter; r += SM_THREADS / 32) {
+            const int bi = r / nouter, oo = r % nouter;
+            const int64_t base = bout[bi] + dv + dz + (v_contig ? offZ0[oo] : offV0[oo]);
+            for (int ii = lane; ii < ninner; ii += 32) out[base + (v_contig ? offV0[ii] : offZ0[ii])] = 0.f;
+          }
+          continue;
+        }
+        float acc[3][6][4];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const int r0 = (mg * 3 + i) * 16 + g;
-            af[i][0] = sA[r0 * SM_PA + k0 + q4];
-            af[i][1] = sA[(r0 + 8) * SM_PA + k0 + q4];
-            af[i][2] = sA[r0 * SM_PA + k0 + q4 + 4];
-            af[i][3] = sA[(r0 + 8) * SM_PA + k0 + q4 + 4];
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+        __syncthreads();   // both A/B buffers free (previous pair's MMAs and output staging done)
+        issue(c0, 0);
+        cp_async_commit();
+        for (int c = c0; c < c1; ++c) {
+          const int buf = (c - c0) & 1;
+          if (c + 1 < c1) {
+            issue(c + 1, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+          } else {
+            cp_async_wait<0>();
+          }
+          __syncthreads();
+          const float* sA = sAb[buf];
+          const float* sB = sBb[buf];
+          for (int k0 = 0; k0 < K1p; k0 += 8) {
+            float af[3][4], bf[6][2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              const int r0 = (mg * 3 + i) * 16 + g;
+              af[i][0] = sA[r0 * SM_PA + k0 + q4];
+              af[i][1] = sA[(r0 + 8) * SM_PA + k0 + q4];
+              af[i][2] = sA[r0 * SM_PA + k0 + q4 + 4];
+              af[i][3] = sA[(r0 + 8) * SM_PA + k0 + q4 + 4];
+            }
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+              const int n = (ng * 6 + j) * 8 + g;
+              bf[j][0] = sB[(k0 + q4) * SM_PB + n];
+              bf[j][1] = sB[(k0 + q4 + 4) * SM_PB + n];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int j = 0; j < 6; ++j) mma3(acc[i][j], af[i], bf[j]);
+          }
+          __syncthreads();   // this buffer is refilled two channels later
+        }
+        // acc (rows (bi,x',y'), cols (v,z,q)) -> sC rows (bi,v,z), cols (x',y',q)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 6; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int m = (mg * 3 + i) * 16 + g + ((r >> 1) << 3);
+              const int n = (ng * 6 + j) * 8 + q4 * 2 + (r & 1);
+              if (m < M1 && n < N1) {
+                int bi = m / K1, xy = m % K1;
+                int q = n % p, vz = n / p;
+                sC[(bi * N2 + vz) * SM_PC + xy * p + q] = acc[i][j][r];
+              }
+            }
+        __syncthreads();
+        // bra: rows (bi, v, z) x cols (v', z'), K = (x', y', q)
+        float d2[5][4];
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) d2[j][r] = 0.f;
+        for (int k0 = 0; k0 < K2p; k0 += 8) {
+          float af[4], bf[5][2];
+          const int r0 = warp * 16 + g;
+          af[0] = sC[r0 * SM_PC + k0 + q4];
+          af[1] = sC[(r0 + 8) * SM_PC + k0 + q4];
+          af[2] = sC[r0 * SM_PC + k0 + q4 + 4];
+          af[3] = sC[(r0 + 8) * SM_PC + k0 + q4 + 4];
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            bf[j][0] = sR[(k0 + q4) * SM_PR + j * 8 + g];
+            bf[j][1] = sR[(k0 + q4 + 4) * SM_PR + j * 8 + g];
           }
 #pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            const int n = (ng * 6 + j) * 8 + g;
-            bf[j][0] = sB[(k0 + q4) * SM_PB + n];
-            bf[j][1] = sB[(k0 + q4 + 4) * SM_PB + n];
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 6; ++j) mma3(acc[i][j], af[i], bf[j]);
+          for (int j = 0; j < 5; ++j) mma3(d2[j], af, bf[j]);
         }
-      }
-      __syncthreads();
-      // acc (rows (bi,x',y'), cols (v,z,q)) -> sC rows (bi,v,z), cols (x',y',q)
+        // stage the output tile in A buffer 0 (free): rows (bi, v, z), cols (v', z')
+        float* st = sAb[0];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
+        for (int j = 0; j < 5; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int m = (mg * 3 + i) * 16 + g + ((r >> 1) << 3);
-            const int n = (ng * 6 + j) * 8 + q4 * 2 + (r & 1);
-            if (m < M1 && n < N1) {
-              int bi = m / K1, xy = m % K1;
-              int q = n % p, vz = n / p;
-              sC[(bi * N2 + vz) * SM_PC + xy * p + q] = acc[i][j][r];
+            const int m = warp * 16 + g + ((r >> 1) << 3);
+            const int n = j * 8 + q4 * 2 + (r & 1);
+            if (m < M2 && n < N2) st[m * SM_PA + n] = d2[j][r];
+          }
+        __syncthreads();
+        // write out: rows over the strided bundle, lanes along the contiguous one
+        if (v_contig) {
+          for (int r = warp; r < nb * nz * nz; r += SM_THREADS / 32) {
+            const int bi = r / (nz * nz), zz = r % (nz * nz), z = zz / nz, zp = zz % nz;
+            const int64_t base = bout[bi] + dv + dz + offZ0[zz];
+            for (int vv = lane; vv < nv * nv; vv += 32) {
+              const int v = vv / nv, vp = vv % nv;
+              out[base + offV0[vv]] = st[(bi * N2 + v * nz + z) * SM_PA + vp * nz + zp];
             }
           }
-      __syncthreads();
-      // bra: rows (bi, v, z) x cols (v', z'), K = (x', y', q)
-      float d2[5][4];
-#pragma unroll
-      for (int j = 0; j < 5; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) d2[j][r] = 0.f;
-      const int K2p = (K2 + 7) & ~7;
-      for (int k0 = 0; k0 < K2p; k0 += 8) {
-        float af[4], bf[5][2];
-        const int r0 = warp * 16 + g;
-        af[0] = sC[r0 * SM_PC + k0 + q4];
-        af[1] = sC[(r0 + 8) * SM_PC + k0 + q4];
-        af[2] = sC[r0 * SM_PC + k0 + q4 + 4];
-        af[3] = sC[(r0 + 8) * SM_PC + k0 + q4 + 4];
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          bf[j][0] = sR[(k0 + q4) * SM_PR + j * 8 + g];
-          bf[j][1] = sR[(k0 + q4 + 4) * SM_PR + j * 8 + g];
-        }
-#pragma unroll
-        for (int j = 0; j < 5; ++j) mma3(d2[j], af, bf[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < 5; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int m = warp * 16 + g + ((r >> 1) << 3);
-          const int n = j * 8 + q4 * 2 + (r & 1);
-          if (m < M2 && n < N2) {
-            int bi = m / N2, vz = m % N2, v = vz / nz, z = vz % nz;
-            int vp = n / nz, zp = n % nz;
-            int64_t b = b0 + bi, t = b / nk, k = b % nk;
-            int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp, Z = ((int64_t)z * o.nzw + zw) * nz + zp;
-            out[t * o_t + k * o_k + V * o_V + Z * o_Z] = d2[j][r];
+        } else {
+          for (int r = warp; r < nb * nv * nv; r += SM_THREADS / 32) {
+            const int bi = r / (nv * nv), vv = r % (nv * nv), v = vv / nv, vp = vv % nv;
+            const int64_t base = bout[bi] + dv + dz + offV0[vv];
+            for (int zz = lane; zz < nz * nz; zz += 32) {
+              const int z = zz / nz, zp = zz % nz;
+              out[base + offZ0[zz]] = st[(bi * N2 + v * nz + z) * SM_PA + vp * nz + zp];
+            }
           }
         }
+      }
     }
   }
 }
@@ -416,7 +507,8 @@ void first_row_tensor(cudaStream_t s, const T* A, const int dA[5], const T* W, c
 
 bool sandwich_mma_fits(const SandOrient& o) {
   const int K1 = o.nx * o.ny, N1 = o.nv * o.nz * o.p, K2 = K1 * o.p, N2 = o.nv * o.nz;
-  return K1 <= 40 && N1 <= 144 && K2 <= 144 && N2 <= 40 && K1 >= 1 && N2 >= 1;
+  return K1 <= 40 && N1 <= 144 && K2 <= 144 && N2 <= 40 && K1 >= 1 && N2 >= 1 && o.nx <= 6 && o.ny <= 6 &&
+         o.nv <= 6 && o.nz <= 6;   // offset tables hold 36 entries
 }
 
 void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const float* in, int64_t i_t,
@@ -427,7 +519,7 @@ void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t 
   const int K1 = o.nx * o.ny, N2 = o.nv * o.nz;
   const int nb_per = std::max(1, std::min(144 / K1, 144 / N2));
   const int64_t nblk = nt * nk;
-  const int64_t grid = (nblk + nb_per - 1) / nb_per;
+  const int64_t grid = (nblk + (int64_t)nb_per * SM_GROUPS - 1) / ((int64_t)nb_per * SM_GROUPS);
   FP_CHECK(grid < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core sandwich: too many blocks");
   const size_t smem = (size_t)SM_FLOATS * sizeof(float);
   static bool attr = false;

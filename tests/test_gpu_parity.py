@@ -41,17 +41,18 @@ def _env(fp, peps, pepo, *, D, w, chi, prec, seed):
 @pytest.mark.parametrize("kind", ["identity", "dense2", "fsm2", "fsm4"])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4), ("tf32x3", 1e-4)])
 def test_c1_3x3_exact_against_brute_force(fp, kind, prec, tol):
+    """3x3, D=2, chi >= the largest rank of any Theta_c: the exact regime (pin (a))."""
     peps = L.random_peps(3, 3, 2, 4, seed=0)
     if kind == "identity":
-        pepo, w = L.identity_pepo(3, 3, 4), 1
+        pepo, w, chi = L.identity_pepo(3, 3, 4), 1, 16
     elif kind == "dense2":
-        pepo, w = L.dense_pepo(3, 3, 4, 2, seed=1), 2
+        pepo, w, chi = L.dense_pepo(3, 3, 4, 2, seed=1), 2, 64
     elif kind == "fsm2":
-        pepo, w = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 0, seed=1)), 2
+        pepo, w, chi = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 0, seed=1)), 2, 64
     else:
-        pepo, w = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 2, seed=1)), 4
+        pepo, w, chi = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 2, seed=1)), 4, 256
     num, den = N.brute_force_expectation(peps, pepo)
-    env = _env(fp, peps, pepo, D=2, w=w, chi=16, prec=prec, seed=9)
+    env = _env(fp, peps, pepo, D=2, w=w, chi=chi, prec=prec, seed=9)
     prm = fp.params(oversample=10, power_iters=0, n_fit=1, exact_svd=1)
     val, sn, ln = env.expect(prm)
     sd, ld = env.norm(prm)
@@ -61,11 +62,16 @@ def test_c1_3x3_exact_against_brute_force(fp, kind, prec, tol):
     assert _rel(val, num / den) < 2 * tol
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4), ("tf32x3", 2e-4)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 1e-5), ("tf32x3", 1e-5)])
 @pytest.mark.parametrize("n_fit", [0, 1])
 def test_truncated_4x4_matches_oracle_algorithm(fp, prec, tol, n_fit):
-    """Truncated regime (chi=12 < exact bonds): same algorithm, same Omega, both sides."""
-    peps = L.random_peps(4, 4, 2, 4, seed=3)
+    """Truncated regime (chi=12 < exact bonds): same algorithm, same Omega, both sides.
+
+    The PEPS has decaying bond weights, so the kept and discarded singular values
+    are separated; with the flat spectra of a plain random PEPS the kept subspace is
+    near-degenerate and FP32-level perturbations move the result by a fraction of the
+    truncation error itself (test_c2_against_stored_oracle covers that case)."""
+    peps = L.decaying_peps(4, 4, 2, 4, seed=3)
     pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=3))
     prm_o = B.RsvdParams(oversample=6, power_iters=2, n_fit=n_fit)
     sn_o, ln_o = B.contract(peps, pepo, 12, prm_o, seed=5, layer=1)
@@ -175,12 +181,17 @@ def test_product_state_closed_form_on_gpu(fp):
     assert abs(val - N.product_state_energy(vecs, ham)) < 1e-9 * max(1.0, abs(val))
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 1e-3), ("tf32x3", 1e-3)])
-def test_c2_against_stored_oracle(fp, prec, tol):
+@pytest.mark.parametrize("decay,prec,tol", [
+    (False, "f64", 1e-8),
+    # flat random-PEPS spectra: FP32 perturbations shift the near-degenerate kept
+    # subspace; the deviation is bounded by the truncation error (~1% here), not by FP32
+    (False, "f32", 2e-2), (False, "tf32x3", 2e-2),
+    (True, "f64", 1e-8), (True, "f32", 1e-5), (True, "tf32x3", 1e-5)])
+def test_c2_against_stored_oracle(fp, decay, prec, tol):
     """4x4, D=4, w=4, chi=64 truncated; oracle values written by tests/golden/make_golden.py."""
-    path = os.path.join(HERE, "golden", "c2_fsm_seed0.json")
+    path = os.path.join(HERE, "golden", "c2_fsm_decay_seed0.json" if decay else "c2_fsm_seed0.json")
     gold = json.load(open(path))
-    peps = L.random_peps(4, 4, 4, 4, seed=gold["peps_seed"])
+    peps = (L.decaying_peps if decay else L.random_peps)(4, 4, 4, 4, seed=gold["peps_seed"])
     pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=gold["ham_seed"]))
     env = _env(fp, peps, pepo, D=4, w=4, chi=64, prec=prec, seed=gold["sketch_seed"])
     val, sn, ln = env.expect(fp.params(10, 2, 0, 1, 0))

@@ -14,7 +14,7 @@ from oracle import network as N
 from synth import lattice as L
 
 
-def _boundary_value(peps, pepo, chi=16):
+def _boundary_value(peps, pepo, chi=256):
     s, lv = B.contract(peps, pepo, chi, B.RsvdParams(exact_svd=True, n_fit=1, power_iters=0), seed=3, layer=1)
     return s * math.exp(lv)
 
@@ -94,3 +94,24 @@ def test_off_by_one_sketch_counter_is_caught():
     good = [int(x[0]) for x in philox4x64_10(tuple(np.array([v], dtype=np.uint64) for v in (1, 0, 0, 0)), key)]
     bad = [int(x[0]) for x in philox4x64_10(tuple(np.array([v], dtype=np.uint64) for v in (0, 0, 0, 0)), key)]
     assert good == raw and bad != raw
+
+
+def test_arbitrary_qr_completion_is_caught(monkeypatch):
+    """Householder's arbitrary completion directions for a rank-deficient Y (the
+    reading the oracle rejects) fail the zero-column pin; an unordered basis of
+    the same span (an SVD) fails the LAPACK-order pin."""
+    import tests.test_oracle_pins as P
+
+    def householder(Y):
+        Q, R = np.linalg.qr(Y)
+        return Q * np.where(np.diag(R) < 0, -1.0, 1.0)[None, :]
+
+    def svd_basis(Y):
+        return np.linalg.svd(Y, full_matrices=False)[0]
+
+    monkeypatch.setattr(B, "orth", householder)
+    with pytest.raises(AssertionError):
+        P.test_orth_dependent_columns_become_zero()
+    monkeypatch.setattr(B, "orth", svd_basis)
+    with pytest.raises(AssertionError):
+        P.test_orth_full_rank_is_lapack_thin_qr()

@@ -95,9 +95,10 @@ def _value(sign, log):
     return sign * math.exp(log)
 
 
-@pytest.mark.parametrize("pepo_kind", ["identity", "dense2", "fsm2", "fsm4"])
-def test_boundary_equals_brute_force_3x3(pepo_kind):
-    """Pin (a): 3x3, D=2, chi=16, exact-rank sketch: the boundary method reproduces <psi|O|psi>."""
+@pytest.mark.parametrize("pepo_kind,chi", [("identity", 16), ("dense2", 64), ("fsm2", 64), ("fsm4", 256)])
+def test_boundary_equals_brute_force_3x3(pepo_kind, chi):
+    """Pin (a): 3x3, D=2, exact-rank sketch and chi >= the largest rank of any Theta_c
+    (B^2 for bundle B = D w D at the middle site): the boundary method reproduces <psi|O|psi>."""
     peps = L.random_peps(3, 3, 2, 4, seed=0)
     if pepo_kind == "identity":
         pepo = L.identity_pepo(3, 3, 4)
@@ -108,9 +109,10 @@ def test_boundary_equals_brute_force_3x3(pepo_kind):
     else:
         pepo = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 2, seed=1))
     num, _ = N.brute_force_expectation(peps, pepo)
-    prm = B.RsvdParams(exact_svd=True, n_fit=1, power_iters=0)
-    s, lv = B.contract(peps, pepo, 16, prm, seed=9, layer=1)
-    assert _value(s, lv) == pytest.approx(num, rel=1e-10)
+    for n_fit in (0, 1):
+        prm = B.RsvdParams(exact_svd=True, n_fit=n_fit, power_iters=0)
+        s, lv = B.contract(peps, pepo, chi, prm, seed=9, layer=1)
+        assert _value(s, lv) == pytest.approx(num, rel=1e-10)
 
 
 def test_boundary_untruncated_4x4_equals_columnwise():
@@ -146,6 +148,37 @@ def _site_setup(seed=0, D=2, w_K=2):
     T = g.standard_normal((5, dU, 6))
     EL = g.standard_normal((3, 5, dL))
     return EL, T, A, W
+
+
+def test_orth_full_rank_is_lapack_thin_qr():
+    """Thin QR of Sec. IV: for full-rank Y the factor is LAPACK's Householder Q
+    with diag(R) > 0 (unique), so the column order and nesting are those of QR."""
+    g = np.random.default_rng(11)
+    Y = g.standard_normal((60, 12)) @ np.diag(np.logspace(0, -5, 12))
+    Qh, R = np.linalg.qr(Y)
+    Qh = Qh * np.where(np.diag(R) < 0, -1.0, 1.0)[None, :]
+    assert np.allclose(B.orth(Y), Qh, atol=1e-12)
+
+
+def test_orth_dependent_columns_become_zero():
+    """A column in the span of the ones before it (exactly, or zero) gives a zero
+    column in place; the others are the QR factor of the independent columns,
+    and the non-zero columns span range(Y)."""
+    g = np.random.default_rng(12)
+    X = g.standard_normal((40, 6))
+    Y = np.column_stack([X[:, 0], X[:, 1], X[:, 0] - 3 * X[:, 1], X[:, 2], np.zeros(40), X[:, 3],
+                         X[:, 2] * 1e-2, X[:, 4]])
+    Q = B.orth(Y)
+    zero = np.abs(Q).sum(axis=0) == 0
+    assert zero.tolist() == [False, False, True, False, True, False, True, False]
+    ind = Y[:, ~zero]
+    Qh, R = np.linalg.qr(ind)
+    Qh = Qh * np.where(np.diag(R) < 0, -1.0, 1.0)[None, :]
+    assert np.allclose(Q[:, ~zero], Qh, atol=1e-12)
+    assert np.allclose(Q @ (Q.T @ Y), Y, atol=1e-12)
+    # a wide matrix has no thin QR in this reading (callers handle that case)
+    with pytest.raises(ValueError):
+        B.orth(np.ones((3, 4)))
 
 
 def test_rsvd_equals_exact_svd_when_sketch_covers_rank():
@@ -196,15 +229,17 @@ def test_zipup_and_fit_canonical_forms():
     T, _ = B.first_row_boundary(peps[0], pepo[0])
     prm = B.RsvdParams(oversample=5, power_iters=1)
     N_, ELs, _, sp = B.zipup(T, peps[1], pepo[1], 12, prm, seed=0, layer=1, row=1)
-    for n in N_[:-1]:
+    for c, n in enumerate(N_[:-1]):
         m = n.reshape(-1, n.shape[2])
         assert np.allclose(m.T @ m, np.eye(m.shape[1]), atol=1e-12)
-        assert np.all(m.sum(axis=0) >= 0)       # sign gauge
+        w = gaussian_sketch(m.shape[0], 1, seed=0, layer=1, stage=2, site=c, row=1)[:, 0]
+        assert np.all(w @ m >= 0)                # sign gauge
     newT, _, _ = B.cbe_fit(T, peps[1], pepo[1], N_, ELs, 12, prm, seed=0, layer=1, row=1)
-    for n in newT[1:]:
+    for c, n in enumerate(newT[1:], start=1):
         m = n.reshape(n.shape[0], -1)
         assert np.allclose(m @ m.T, np.eye(m.shape[0]), atol=1e-12)
-        assert np.all(m.sum(axis=1) >= 0)
+        w = gaussian_sketch(m.shape[1], 1, seed=0, layer=1, stage=2, site=c, row=1)[:, 0]
+        assert np.all(m @ w >= 0)
     assert abs(np.linalg.norm(newT[0]) - 1) < 1e-12
 
 
