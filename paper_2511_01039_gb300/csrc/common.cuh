@@ -169,6 +169,12 @@ void scale_by_inv(cudaStream_t s, T* x, int64_t n, const double* nrm);
 
 template <class T>
 void permute3(cudaStream_t s, const T* in, T* out, int64_t d0, int64_t d1, int64_t d2, int p0, int p1, int p2);
+// dst[c * ld_dst + r] = src[r * ld_src + c] for r < rows, c < cols; zero for rows <= r < ld_dst
+template <class T>
+void transpose_pad(cudaStream_t s, const T* src, int64_t rows, int64_t cols, int64_t ld_src, T* dst, int64_t ld_dst);
+// dst (col-major rows x cols) = (T) src (row-major rows x cols)
+template <class T>
+void convert_f64_t(cudaStream_t s, const double* src, int64_t rows, int64_t cols, T* dst);
 
 template <class T>
 void fill(cudaStream_t s, T* x, int64_t n, T v);

@@ -170,8 +170,11 @@ struct Engine : EngineBase {
 
   // ---------------------------------------------------------------- GEMMs
   // C = A B^T, A [M][lda], B [N][ldb], both k-contiguous
-  void big_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C, OutMap om) {
-    flops += 2.0 * (double)M * (double)N * (double)K;
+  // count = false for the products of the QR / SVD steps, which the algorithmic
+  // flop count of the contraction leaves out
+  void big_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C, OutMap om,
+                bool count = true) {
+    if (count) flops += 2.0 * (double)M * (double)N * (double)K;
     // tensor cores for every contraction with at least one full 128x128x32 tile and
     // 16-byte aligned rows; smaller edge contractions stay on the CUDA cores (FP32)
     if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && gemm_tc_supported(M, N, K, lda, ldb) &&
@@ -199,6 +202,23 @@ struct Engine : EngineBase {
     int64_t am = ta ? lda : 1, ak = ta ? 1 : lda;
     int64_t bn = tb ? 1 : ldb, bk = tb ? ldb : 1;
     gemm_simt<T>(s, m, n, k, alpha, A, am, ak, B, bn, bk, beta, C, out_colmajor(m, n, ldc));
+  }
+  // out (m x n, col-major, ld ldo) = X (m x k, col-major, ld ldx) S (k x n, col-major, ld lds): a tall
+  // matrix times a small one. In 3xTF32 mode with at least one full tile this runs on the tensor
+  // cores through K-major copies (X transposed, S with its rows padded to a multiple of 4).
+  void mm_right(int64_t m, int n, int k, const T* X, int64_t ldx, const T* S, int64_t lds, T* out, int64_t ldo) {
+    const int kp = (k + 3) & ~3;
+    if (sizeof(T) == 4 && mode == FPEPS_TF32X3 && gemm_tc_supported(m, n, k, kp, kp)) {
+      Arena ar = arena();
+      T* Xt = ar.get_n<T>((size_t)m * kp);
+      transpose_pad<T>(s, X, k, m, ldx, Xt, kp);
+      T* St = ar.get_n<T>((size_t)n * kp);
+      if (kp != k) FP_CUDA(cudaMemsetAsync(St, 0, sizeof(T) * n * kp, s));
+      FP_CUDA(cudaMemcpy2DAsync(St, sizeof(T) * kp, S, sizeof(T) * lds, sizeof(T) * k, n, cudaMemcpyDeviceToDevice, s));
+      big_gemm(m, n, k, Xt, kp, St, kp, out, out_colmajor(m, n, ldo), false);
+      return;
+    }
+    mm(m, n, k, T(1), X, false, ldx, S, false, lds, T(0), out, ldo);
   }
   void mm64(int64_t m, int64_t n, int64_t k, const double* A, bool ta, int64_t lda, const double* B, bool tb,
             int64_t ldb, double* C, int64_t ldc) {
@@ -425,9 +445,9 @@ struct Engine : EngineBase {
     T* Bt = ar.get_n<T>((int64_t)k * k);
     double* Rinv = ar.get_n<double>((int64_t)k * k);
     tri_inverse_upper_f64(s, G, k, Rinv);
-    convert_f64<T>(s, Rinv, Bt, (int64_t)k * k);
-    // Q(m, j) = sum_i Y(m, i) Rinv(i, j);  Rinv row-major
-    gemm_simt<T>(s, m, k, k, T(1), Y, 1, m, Bt, 1, k, T(0), Q, out_colmajor(m, k, m));
+    convert_f64_t<T>(s, Rinv, k, k, Bt);   // Rinv is row-major; Bt col-major
+    // Q(m, j) = sum_i Y(m, i) Rinv(i, j)
+    mm_right(m, k, k, Y, m, Bt, k, Q, m);
     if (R) FP_CUDA(cudaMemcpyAsync(R, G, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
   }
 
@@ -493,7 +513,7 @@ struct Engine : EngineBase {
     T* Vt = ar.get_n<T>((int64_t)k * k);
     convert_f64<T>(s, Vs, Vt, (int64_t)k * k);
     r.QbW = ar.get_n<T>(n * k);
-    mm(n, k, k, T(1), Qz, false, n, Vt, false, k, T(0), r.QbW, n);
+    mm_right(n, k, k, Qz, n, Vt, k, r.QbW, n);
     r.sigma.resize(k);
     FP_CUDA(cudaMemcpyAsync(r.sigma.data(), sg, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     FP_CUDA(cudaStreamSynchronize(s));
@@ -619,7 +639,7 @@ struct Engine : EngineBase {
       T* Ut = ar.get_n<T>((int64_t)k * k);
       convert_f64<T>(s, r.U, Ut, (int64_t)k * k);
       T* N = rowmem.get_n<T>(rows * chi_c);
-      mm(rows, chi_c, k, T(1), r.Q, false, rows, Ut, false, k, T(0), N, rows);
+      mm_right(rows, chi_c, k, r.Q, rows, Ut, k, N, rows);
       // sign gauge: weights from the sketch generator (stage 2) over the (a, Dn)
       // flat index; rows are stored Dn-major with a fastest
       double* sgn = ar.get_n<double>(chi_c);
@@ -849,7 +869,7 @@ struct Engine : EngineBase {
       convert_f64<T>(s, Vs, Urt, (int64_t)j * j);
       // new right isometry N_c^T = V' W[:, :keep]  ->  [keep][Dn][a_c]
       T* Nc = (T*)e->al.get(sizeof(T) * cols_a * keep);
-      mm(cols_a, keep, j, T(1), Vp, false, cols_a, Wt, false, j, T(0), Nc, cols_a);
+      mm_right(cols_a, keep, j, Vp, cols_a, Wt, j, Nc, cols_a);
       double* sgn = ar.get_n<double>(keep);
       T* gw = ar.get_n<T>(cols_a);
       gaussian_sketch<T>(s, gw, cols_a, 1, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16),
@@ -863,14 +883,14 @@ struct Engine : EngineBase {
       double* scl = ar.get_n<double>(keep);
       mul_vec(s, sg, sgn, scl, keep);
       T* Mv = ar.get_n<T>(rows_a * keep);
-      mm(rows_a, keep, j, T(1), Qm, false, rows_a, Urt, false, j, T(0), Mv, rows_a);
+      mm_right(rows_a, keep, j, Qm, rows_a, Urt, j, Mv, rows_a);
       scale_cols<T>(s, Mv, rows_a, keep, rows_a, scl);
       Arena mnew = arena();
       T* Mnext = mnew.get_n<T>(rows_a * keep);
       permute3<T>(s, Mv, Mnext, keep, Dnl, a2, 2, 1, 0);
       // ER_c vectors = ER' W[:, :keep] diag(sign)  -> [keep][L][t]
       T* erv = ar.get_n<T>(nER * keep);
-      mm(nER, keep, j, T(1), ERp, false, nER, Wt, false, j, T(0), erv, nER);
+      mm_right(nER, keep, j, ERp, nER, Wt, j, erv, nER);
       scale_cols<T>(s, erv, nER, keep, nER, sgn);
       double nrm = host_norm(erv, nER * keep);
       FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "right environment vanished");

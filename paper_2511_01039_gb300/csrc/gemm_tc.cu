@@ -7,7 +7,8 @@
 // (boundary x vectors, environment x vectors). FP32 inputs are split on chip
 // into x = hi + lo and the product is a_hi b_hi + a_hi b_lo + a_lo b_hi with
 // FP32 accumulation in TMEM:
-//   mode 2 (3xTF32): hi = x rounded to TF32 (10-bit mantissa), lo = x - hi,
+//   mode 2 (3xTF32): hi = x rounded to TF32 (10-bit mantissa), lo = x - hi
+//                    rounded to TF32 as well (|x - hi - lo| <= 2^-22 |x|),
 //                    kind::tf32 MMAs on the 32-bit tiles.
 // The kernel is persistent (one CTA per SM walks a static tile schedule) with
 // warp roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
@@ -314,10 +315,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
           uint4* dlo = e < TILE_A / 16 ? alo + e : blo + (e - TILE_A / 16);
           uint4 v = *src;
           uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-          uint4 l = make_uint4(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x)),
-                               __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y)),
-                               __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z)),
-                               __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w)));
+          uint4 l = make_uint4(tf32_round(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x))),
+                               tf32_round(__float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y))),
+                               tf32_round(__float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z))),
+                               tf32_round(__float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w))));
           *src = h;
           *dlo = l;
         }

@@ -13,6 +13,7 @@
 // path always applies it to the transposed triangular factor of a QR (the
 // preconditioned form of Drmac and Veselic 2008), where it converges in about
 // ten sweeps; the sweep count is capped at 30.
+#include <cstdio>
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -401,6 +402,55 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k
 // The same method spread over the whole GPU: one warp per column pair, a grid
 // barrier (cooperative launch) between rounds. ws[0..3]: sweep rotation
 // counters (two, alternating) and the squared Frobenius norm.
+// One rotation of the pair (p, q) by one warp: both columns of M and of V are
+// loaded into registers at once (NI elements per lane), so a round costs one
+// memory latency instead of one per 32 elements. Returns true if it rotated.
+template <int NI>
+__device__ __forceinline__ bool jacobi_rotate_pair(double* __restrict__ mp, double* __restrict__ mq,
+                                                   double* __restrict__ vp, double* __restrict__ vq, int k, int lane,
+                                                   double eps, double tiny) {
+  double x[NI], y[NI], a[NI], b[NI];
+#pragma unroll
+  for (int t = 0; t < NI; ++t) {
+    const int i = lane + 32 * t;
+    const bool in = i < k;
+    x[t] = in ? mp[i] : 0.0;
+    y[t] = in ? mq[i] : 0.0;
+    a[t] = in ? vp[i] : 0.0;
+    b[t] = in ? vq[i] : 0.0;
+  }
+  double al = 0, be = 0, ga = 0;
+#pragma unroll
+  for (int t = 0; t < NI; ++t) {
+    al = fma(x[t], x[t], al);
+    be = fma(y[t], y[t], be);
+    ga = fma(x[t], y[t], ga);
+  }
+  for (int o = 16; o; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (ga == 0.0 || fmin(al, be) <= tiny || fabs(ga) <= eps * sqrt(al) * sqrt(be)) return false;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+#pragma unroll
+  for (int u = 0; u < NI; ++u) {
+    const int i = lane + 32 * u;
+    if (i < k) {
+      mp[i] = c * x[u] - sn * y[u];
+      mq[i] = sn * x[u] + c * y[u];
+      vp[i] = c * a[u] - sn * b[u];
+      vq[i] = sn * a[u] + c * b[u];
+    }
+  }
+  return true;
+}
+
+// Cooperative one-sided Jacobi over the whole GPU: round-robin pair schedule,
+// one warp per pair, a grid barrier between rounds. NI * 32 >= k.
+template <int NI>
 __global__ void __launch_bounds__(256) k_jacobi_svd_coop(double* M, double* V, int k, int max_sweeps, double eps,
                                                          unsigned long long* ws) {
   namespace cg = cooperative_groups;
@@ -432,36 +482,16 @@ __global__ void __launch_bounds__(256) k_jacobi_svd_coop(double* M, double* V, i
         int a = rr_player(pr, round, kk), b = rr_player(kk - 1 - pr, round, kk);
         int p = min(a, b), q = max(a, b);
         if (q >= k) continue;
-        double* mp = M + (int64_t)p * k;
-        double* mq = M + (int64_t)q * k;
-        double al = 0, be = 0, ga = 0;
-        for (int i = lane; i < k; i += 32) {
-          double x = mp[i], y = mq[i];
-          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
-        }
-        for (int o = 16; o; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (ga == 0.0 || fmin(al, be) <= tiny || fabs(ga) <= eps * sqrt(al) * sqrt(be)) continue;
-        double zeta = (be - al) / (2.0 * ga);
-        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-        for (int i = lane; i < k; i += 32) {
-          double x = mp[i], y = mq[i];
-          mp[i] = c * x - sn * y;
-          mq[i] = sn * x + c * y;
-          double vx = V[(int64_t)p * k + i], vy = V[(int64_t)q * k + i];
-          V[(int64_t)p * k + i] = c * vx - sn * vy;
-          V[(int64_t)q * k + i] = sn * vx + c * vy;
-        }
-        if (lane == 0) atomicAdd(&ws[sweep & 1], 1ull);
+        if (jacobi_rotate_pair<NI>(M + (int64_t)p * k, M + (int64_t)q * k, V + (int64_t)p * k, V + (int64_t)q * k, k,
+                                   lane, eps, tiny) &&
+            lane == 0)
+          atomicAdd(&ws[sweep & 1], 1ull);
       }
       grid.sync();
     }
     const unsigned long long rot = *(volatile unsigned long long*)&ws[sweep & 1];
     grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) ws[3] = (unsigned long long)(sweep + 1);
     if (rot == 0) break;
   }
 }
@@ -527,6 +557,34 @@ __global__ void k_scale_inv(T* x, int64_t n, const double* nrm) {
   const double inv = 1.0 / nrm[0];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     x[e] = (T)((double)x[e] * inv);
+}
+
+// dst[c * ld_dst + r] = src[r * ld_src + c] (r < rows, c < cols), zero for
+// rows <= r < ld_dst: a padded transpose through 32 x 33 shared tiles.
+template <class T>
+__global__ void k_transpose_pad(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld_src,
+                                T* __restrict__ dst, int64_t ld_dst) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + tx;
+    tile[i][tx] = (r < rows && c < cols) ? src[r * ld_src + c] : T(0);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t c = c0 + i, r = r0 + tx;
+    if (c < cols && r < ld_dst) dst[c * ld_dst + r] = tile[tx][i];
+  }
+}
+
+// dst[c * rows + r] = (T) src[r * cols + c]
+template <class T>
+__global__ void k_convert_f64_t(const double* __restrict__ src, int64_t rows, int64_t cols, T* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, r = e % rows;
+    dst[e] = (T)src[r * cols + c];
+  }
 }
 
 template <class T>
@@ -697,16 +755,20 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
     k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15 * sqrt((double)k), info);
     FP_LAUNCH();
   } else {
-    static int max_blocks = -1;
-    if (max_blocks < 0) {
+    // registers per lane: NI = ceil(k / 32) elements of each of the four columns
+    void* fn = k <= 256 ? (void*)k_jacobi_svd_coop<8>
+                        : k <= 576 ? (void*)k_jacobi_svd_coop<18> : (void*)k_jacobi_svd_coop<32>;
+    const int ti = k <= 256 ? 0 : (k <= 576 ? 1 : 2);
+    static int max_blocks[3] = {-1, -1, -1};
+    if (max_blocks[ti] < 0) {
       int dev = 0, sms = 0, per = 0;
       FP_CUDA(cudaGetDevice(&dev));
       FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_svd_coop, 256, 0));
-      max_blocks = sms * std::max(per, 0);
+      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0));
+      max_blocks[ti] = sms * std::max(per, 0);
     }
     int pairs = (k + 1) / 2;
-    int blocks = std::min(max_blocks, (pairs + 7) / 8);
+    int blocks = std::min(max_blocks[ti], (pairs + 7) / 8);
     FP_CHECK(blocks >= 1, FPEPS_ERR_CUDA, "svd: no co-resident blocks");
     unsigned long long* ws = (unsigned long long*)ws_dev;
     int max_sweeps = 30;
@@ -714,9 +776,16 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
     void* args[] = {&Mat, &V, &k, &max_sweeps, &eps, &ws};
     ProfToken pt = prof_begin(PROF_FACTOR, s, 0.0, 16.0 * k * k);
     count_launch();
-    FP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_svd_coop, blocks, 256, args, 0, s));
+    FP_CUDA(cudaLaunchCooperativeKernel(fn, blocks, 256, args, 0, s));
     prof_end(pt, s);
     FP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+    static const bool trace = getenv("FPEPS_TRACE_SVD") != nullptr;   // diagnostics: sweeps used
+    if (trace) {
+      unsigned long long sw = 0;
+      FP_CUDA(cudaMemcpyAsync(&sw, ws + 3, sizeof(sw), cudaMemcpyDeviceToHost, s));
+      FP_CUDA(cudaStreamSynchronize(s));
+      fprintf(stderr, "[fpeps] jacobi k=%d sweeps=%llu\n", k, sw);
+    }
   }
   k_svd_finish<<<1, 1024, 0, s>>>(Mat, k, U, sigma, order);
   FP_LAUNCH();
@@ -745,6 +814,21 @@ void frob_norm_f64(cudaStream_t s, const T* x, int64_t n, double* out) {
 template <class T>
 void scale_by_inv(cudaStream_t s, T* x, int64_t n, const double* nrm) {
   k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(x, n, nrm);
+  FP_LAUNCH();
+}
+
+template <class T>
+void transpose_pad(cudaStream_t s, const T* src, int64_t rows, int64_t cols, int64_t ld_src, T* dst, int64_t ld_dst) {
+  if (rows <= 0 || cols <= 0) return;
+  const int64_t gy = (ld_dst + 31) / 32, gx = (cols + 31) / 32;
+  FP_CHECK(gy < 65536, FPEPS_ERR_UNSUPPORTED, "transpose: too many rows");
+  k_transpose_pad<T><<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(src, rows, cols, ld_src, dst, ld_dst);
+  FP_LAUNCH();
+}
+
+template <class T>
+void convert_f64_t(cudaStream_t s, const double* src, int64_t rows, int64_t cols, T* dst) {
+  k_convert_f64_t<T><<<grid_for(rows * cols), 256, 0, s>>>(src, rows, cols, dst);
   FP_LAUNCH();
 }
 
@@ -808,6 +892,8 @@ void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst) {
   template void frob_norm_f64<T>(cudaStream_t, const T*, int64_t, double*);                                  \
   template void scale_by_inv<T>(cudaStream_t, T*, int64_t, const double*);                                   \
   template void permute3<T>(cudaStream_t, const T*, T*, int64_t, int64_t, int64_t, int, int, int);            \
+  template void transpose_pad<T>(cudaStream_t, const T*, int64_t, int64_t, int64_t, T*, int64_t);            \
+  template void convert_f64_t<T>(cudaStream_t, const double*, int64_t, int64_t, T*);                         \
   template void fill<T>(cudaStream_t, T*, int64_t, T);                                                        \
   template void check_finite<T>(cudaStream_t, const T*, int64_t, int*);                                      \
   template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, const T*, double*);                         \

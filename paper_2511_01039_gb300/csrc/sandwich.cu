@@ -196,13 +196,13 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
 // nearest) and the three products hi*hi + hi*lo + lo*hi accumulate in FP32.
 constexpr int SM_MT = 9, SM_PA = 44, SM_PB = 152, SM_PC = 148, SM_PR = 40;
 constexpr int SM_THREADS = 288;   // 9 warps
-constexpr int SM_FLOATS = 2 * 144 * SM_PA + 2 * 40 * SM_PB + 144 * SM_PC + 144 * SM_PR + 2 * (2 * 144 + 4 * 36) + 36;
+constexpr int SM_A = 144 * SM_PA, SM_B = 40 * SM_PB, SM_C = 144 * SM_PC, SM_R = 144 * SM_PR;
+constexpr int SM_TILE_FLOATS = 2 * SM_A + 2 * SM_B + SM_C + SM_R;
+constexpr int SM_FLOATS = SM_TILE_FLOATS + 2 * (144 + 144) + 144;   // + int64 row tables, int32 A offsets
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// round to the nearest TF32 value, ties away from zero, with integer operations
+// on the bit pattern (sign-magnitude: adding half an ulp to the magnitude)
+__device__ __forceinline__ uint32_t to_tf32(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   hi = to_tf32(x);
   lo = to_tf32(x - __uint_as_float(hi));
@@ -213,26 +213,32 @@ __device__ __forceinline__ void mma_tf32_16x8x8(float* d, const uint32_t* a, con
                : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
-// 3xTF32 product from fp32 fragments
-__device__ __forceinline__ void mma3(float* d, const float* af, const float* bf) {
-  uint32_t ah[4], al[4], bh[2], bl[2];
+// 3xTF32 products of split fragments: the three passes run over all tiles in
+// turn, so consecutive MMAs never update the same accumulator
+template <int MI, int NJ>
+__device__ __forceinline__ void mma3_tiles(float (*acc)[NJ][4], const uint32_t (*ah)[4], const uint32_t (*al)[4],
+                                           const uint32_t (*bh)[2], const uint32_t (*bl)[2]) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) split_tf32(af[i], ah[i], al[i]);
+  for (int i = 0; i < MI; ++i)
 #pragma unroll
-  for (int i = 0; i < 2; ++i) split_tf32(bf[i], bh[i], bl[i]);
-  mma_tf32_16x8x8(d, al, bh);
-  mma_tf32_16x8x8(d, ah, bl);
-  mma_tf32_16x8x8(d, ah, bh);
+    for (int j = 0; j < NJ; ++j) mma_tf32_16x8x8(acc[i][j], al[i], bh[j]);
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) mma_tf32_16x8x8(acc[i][j], ah[i], bl[j]);
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) mma_tf32_16x8x8(acc[i][j], ah[i], bh[j]);
 }
 
-// Offsets are tabulated once per CTA (block bases, bundle rows and columns;
-// the PEPO channel only shifts them by a constant), the gathers of a channel
-// are issued as cp.async copies into one of two A/B buffers while the MMAs of
-// the previous channel run, and the output tile is staged so that it is
-// written in contiguous runs.
-constexpr int SM_GROUPS = 8;   // groups of nb_per blocks handled by one CTA
-constexpr int SM_TILE_FLOATS = 2 * 144 * SM_PA + 2 * 40 * SM_PB + 144 * SM_PC + 144 * SM_PR;
-
+// The kernel is persistent (one CTA per SM walks the groups of nb_per blocks).
+// Per group, offset tables give the input position of every (block, ket column
+// (x, y)) and the output position of every (block, ket (v, z)); each thread keeps
+// one bra position (x', y') for the gathers and one (v', z') for the stores, with
+// the contiguous bundle index fastest across the lanes. The gathers of a channel
+// are cp.async copies into one of two A/B buffers, issued while the MMAs of the
+// previous channel run; the output tile is staged in shared memory.
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
@@ -249,22 +255,18 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, int64_t nt, int64_t nk, int nb_per,
-                                                                const float* __restrict__ in, int64_t i_t,
-                                                                int64_t i_k, int64_t i_X, int64_t i_Y,
+                                                                int64_t ngroups, const float* __restrict__ in,
+                                                                int64_t i_t, int64_t i_k, int64_t i_X, int64_t i_Y,
                                                                 float* __restrict__ out, int64_t o_t, int64_t o_k,
                                                                 int64_t o_V, int64_t o_Z) {
   extern __shared__ float sm[];
-  float* sAb[2] = {sm, sm + 144 * SM_PA};                       // [144][SM_PA] rows (b, x', y'), cols (x, y)
-  float* sBb[2] = {sm + 2 * 144 * SM_PA, sm + 2 * 144 * SM_PA + 40 * SM_PB};   // [40][SM_PB] (x,y) x (v,z,q)
-  float* sC = sm + 2 * 144 * SM_PA + 2 * 40 * SM_PB;            // [144][SM_PC] rows (b, v, z), cols (x', y', q)
-  float* sR = sC + 144 * SM_PC;                                 // [144][SM_PR] rows (x', y', q), cols (v', z')
-  int64_t* bin = reinterpret_cast<int64_t*>(sR + 144 * SM_PR);  // [144] block input bases
-  int64_t* bout = bin + 144;                                    // [144] block output bases
-  int64_t* rowX0 = bout + 144;                                  // [36] (x, x') at channel x_w = 0
-  int64_t* colY0 = rowX0 + 36;                                  // [36] (y, y') at y_w = 0
-  int64_t* offV0 = colY0 + 36;                                  // [36] (v, v') at v_w = 0
-  int64_t* offZ0 = offV0 + 36;                                  // [36] (z, z') at z_w = 0
-  int* dyy = reinterpret_cast<int*>(offZ0 + 36);                // [36] A-tile offset of (y, y')
+  float* const sA0 = sm;                    // A buffer b at sA0 + b * SM_A: rows (blk, x', y'), cols (x, y)
+  float* const sB0 = sm + 2 * SM_A;         // B buffer b at sB0 + b * SM_B: rows (x, y), cols (v, z, q)
+  float* const sC = sB0 + 2 * SM_B;         // rows (blk, v, z), cols (x', y', q)
+  float* const sR = sC + SM_C;              // rows (x', y', q), cols (v', z')
+  int64_t* const rowIn = reinterpret_cast<int64_t*>(sR + SM_R);   // [blk][x y] input offset
+  int64_t* const rowOut = rowIn + 144;                            // [blk][v z] output offset
+  int* const dstA = reinterpret_cast<int*>(rowOut + 144);         // [blk][x y] A-tile offset
   const float* AW = static_cast<const float*>(o.d_aw);
   const float* AR = static_cast<const float*>(o.d_ar);
   const int nx = o.nx, ny = o.ny, nv = o.nv, nz = o.nz, p = o.p;
@@ -274,19 +276,24 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
   const int g = lane >> 2, q4 = lane & 3;
   const int mg = warp / 3, ng = warp % 3;
   const int64_t nblk = nt * nk;
-  const bool v_contig = (o_V == 1);
   const bool aw16 = (N1 % 4) == 0 && ((uintptr_t)AW % 16) == 0;
 
+  // this thread's gather slot: bra position (x', y'), lanes along the contiguous one
+  const int gstep = SM_THREADS / K1, gslot = tid % K1, g0 = tid / K1;
+  const bool gact = tid < gstep * K1;
+  const bool x_fast = (i_X == 1 && i_Y != 1);
+  const int gxp = x_fast ? gslot % nx : gslot / ny, gyp = x_fast ? gslot / nx : gslot % ny;
+  const int64_t gpart = gxp * i_X + gyp * i_Y;
+  const int grow = (gxp * ny + gyp) * SM_PA;
+  // this thread's store slot: (v', z'), lanes along the contiguous one
+  const int wstep = SM_THREADS / N2, wslot = tid % N2, w0 = tid / N2;
+  const bool wact = tid < wstep * N2;
+  const bool v_fast = (o_V == 1 && o_Z != 1);
+  const int wvp = v_fast ? wslot % nv : wslot / nz, wzp = v_fast ? wslot / nv : wslot % nz;
+  const int64_t wpart = wvp * o_V + wzp * o_Z;
+  const int wcol = wvp * nz + wzp;
+
   for (int e = tid; e < SM_TILE_FLOATS; e += SM_THREADS) sm[e] = 0.f;
-  if (tid < 36) {
-    if (tid < nx * nx) rowX0[tid] = ((int64_t)(tid / nx) * o.nxw * nx + tid % nx) * i_X;
-    if (tid < ny * ny) {
-      colY0[tid] = ((int64_t)(tid / ny) * o.nyw * ny + tid % ny) * i_Y;
-      dyy[tid] = (tid % ny) * SM_PA + tid / ny;
-    }
-    if (tid < nv * nv) offV0[tid] = ((int64_t)(tid / nv) * o.nvw * nv + tid % nv) * o_V;
-    if (tid < nz * nz) offZ0[tid] = ((int64_t)(tid / nz) * o.nzw * nz + tid % nz) * o_Z;
-  }
   __syncthreads();
   for (int e = tid; e < K2 * N2; e += SM_THREADS) {
     int r = e / N2, c = e % N2;            // r = (x', y', q), c = (v', z')
@@ -295,32 +302,34 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
     sR[r * SM_PR + c] = AR[(((xp * ny + yp) * nv + vp) * nz + zp) * p + q];
   }
 
-  for (int grp = 0; grp < SM_GROUPS; ++grp) {
-    const int64_t b0 = ((int64_t)blockIdx.x * SM_GROUPS + grp) * nb_per;
-    if (b0 >= nblk) break;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int64_t b0 = grp * nb_per;
     const int nb = (int)min((int64_t)nb_per, nblk - b0);
     const int M1 = nb * K1, M2 = nb * N2;
-    __syncthreads();   // previous group done with every table and tile
-    for (int bi = tid; bi < nb; bi += SM_THREADS) {
+    __syncthreads();   // the previous group is done with every table and tile
+    for (int e = tid; e < M1; e += SM_THREADS) {
+      const int bi = e / K1, col = e % K1, x = col / ny, y = col % ny;
       const int64_t b = b0 + bi, t = b / nk, k = b % nk;
-      bin[bi] = t * i_t + k * i_k;
-      bout[bi] = t * o_t + k * o_k;
+      rowIn[e] = t * i_t + k * i_k + (int64_t)x * o.nxw * nx * i_X + (int64_t)y * o.nyw * ny * i_Y;
+      dstA[e] = bi * K1 * SM_PA + col;
+    }
+    for (int e = tid; e < M2; e += SM_THREADS) {
+      const int bi = e / N2, vz = e % N2, v = vz / nz, z = vz % nz;
+      const int64_t b = b0 + bi, t = b / nk, k = b % nk;
+      rowOut[e] = t * o_t + k * o_k + (int64_t)v * o.nvw * nv * o_V + (int64_t)z * o.nzw * nz * o_Z;
     }
     __syncthreads();
 
     // gathers of channel c into buffer buf (cp.async)
     auto issue = [&](int c, int buf) {
       const int xw = o.d_ch[4 * c + 0], yw = o.d_ch[4 * c + 1];
-      const int64_t dx = (int64_t)xw * nx * i_X, dy = (int64_t)yw * ny * i_Y;
-      float* A = sAb[buf];
-      for (int r = warp; r < nb * nx * nx; r += SM_THREADS / 32) {
-        const int bi = r / (nx * nx), xx = r % (nx * nx), x = xx / nx, xp = xx % nx;
-        const float* src = in + bin[bi] + rowX0[xx] + dx + dy;
-        float* dst = A + (bi * K1 + xp * ny) * SM_PA + x * ny;
-        for (int yy = lane; yy < ny * ny; yy += 32) cp_async4(dst + dyy[yy], src + colY0[yy]);
+      if (gact) {
+        const float* src = in + (int64_t)xw * nx * i_X + (int64_t)yw * ny * i_Y + gpart;
+        float* A = sA0 + buf * SM_A + grow;
+        for (int e = g0; e < M1; e += gstep) cp_async4(A + dstA[e], src + rowIn[e]);
       }
       const float* awc = AW + (int64_t)c * K1 * N1;
-      float* Bm = sBb[buf];
+      float* Bm = sB0 + buf * SM_B;
       if (aw16) {
         const int n4 = N1 / 4;
         for (int e = tid; e < K1 * n4; e += SM_THREADS) {
@@ -337,14 +346,10 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
       for (int zw = 0; zw < o.nzw; ++zw) {
         const int pair = vw * o.nzw + zw;
         const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
-        const int64_t dv = (int64_t)vw * nv * o_V, dz = (int64_t)zw * nz * o_Z;
+        const int64_t obase = (int64_t)vw * nv * o_V + (int64_t)zw * nz * o_Z + wpart;
         if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
-          const int ninner = v_contig ? nv * nv : nz * nz, nouter = v_contig ? nz * nz : nv * nv;
-          for (int r = warp; r < nb * nouter; r += SM_THREADS / 32) {
-            const int bi = r / nouter, oo = r % nouter;
-            const int64_t base = bout[bi] + dv + dz + (v_contig ? offZ0[oo] : offV0[oo]);
-            for (int ii = lane; ii < ninner; ii += 32) out[base + (v_contig ? offV0[ii] : offZ0[ii])] = 0.f;
-          }
+          if (wact)
+            for (int e = w0; e < M2; e += wstep) out[rowOut[e] + obase] = 0.f;
           continue;
         }
         float acc[3][6][4];
@@ -367,28 +372,25 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
             cp_async_wait<0>();
           }
           __syncthreads();
-          const float* sA = sAb[buf];
-          const float* sB = sBb[buf];
+          const float* sA = sA0 + buf * SM_A;
+          const float* sB = sB0 + buf * SM_B;
           for (int k0 = 0; k0 < K1p; k0 += 8) {
-            float af[3][4], bf[6][2];
+            uint32_t ah[3][4], al[3][4], bh[6][2], bl[6][2];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
               const int r0 = (mg * 3 + i) * 16 + g;
-              af[i][0] = sA[r0 * SM_PA + k0 + q4];
-              af[i][1] = sA[(r0 + 8) * SM_PA + k0 + q4];
-              af[i][2] = sA[r0 * SM_PA + k0 + q4 + 4];
-              af[i][3] = sA[(r0 + 8) * SM_PA + k0 + q4 + 4];
+              split_tf32(sA[r0 * SM_PA + k0 + q4], ah[i][0], al[i][0]);
+              split_tf32(sA[(r0 + 8) * SM_PA + k0 + q4], ah[i][1], al[i][1]);
+              split_tf32(sA[r0 * SM_PA + k0 + q4 + 4], ah[i][2], al[i][2]);
+              split_tf32(sA[(r0 + 8) * SM_PA + k0 + q4 + 4], ah[i][3], al[i][3]);
             }
 #pragma unroll
             for (int j = 0; j < 6; ++j) {
               const int n = (ng * 6 + j) * 8 + g;
-              bf[j][0] = sB[(k0 + q4) * SM_PB + n];
-              bf[j][1] = sB[(k0 + q4 + 4) * SM_PB + n];
+              split_tf32(sB[(k0 + q4) * SM_PB + n], bh[j][0], bl[j][0]);
+              split_tf32(sB[(k0 + q4 + 4) * SM_PB + n], bh[j][1], bl[j][1]);
             }
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int j = 0; j < 6; ++j) mma3(acc[i][j], af[i], bf[j]);
+            mma3_tiles<3, 6>(acc, ah, al, bh, bl);
           }
           __syncthreads();   // this buffer is refilled two channels later
         }
@@ -409,57 +411,38 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
             }
         __syncthreads();
         // bra: rows (bi, v, z) x cols (v', z'), K = (x', y', q)
-        float d2[5][4];
+        float d2[1][5][4];
 #pragma unroll
         for (int j = 0; j < 5; ++j)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) d2[j][r] = 0.f;
+          for (int r = 0; r < 4; ++r) d2[0][j][r] = 0.f;
         for (int k0 = 0; k0 < K2p; k0 += 8) {
-          float af[4], bf[5][2];
+          uint32_t ah[1][4], al[1][4], bh[5][2], bl[5][2];
           const int r0 = warp * 16 + g;
-          af[0] = sC[r0 * SM_PC + k0 + q4];
-          af[1] = sC[(r0 + 8) * SM_PC + k0 + q4];
-          af[2] = sC[r0 * SM_PC + k0 + q4 + 4];
-          af[3] = sC[(r0 + 8) * SM_PC + k0 + q4 + 4];
+          split_tf32(sC[r0 * SM_PC + k0 + q4], ah[0][0], al[0][0]);
+          split_tf32(sC[(r0 + 8) * SM_PC + k0 + q4], ah[0][1], al[0][1]);
+          split_tf32(sC[r0 * SM_PC + k0 + q4 + 4], ah[0][2], al[0][2]);
+          split_tf32(sC[(r0 + 8) * SM_PC + k0 + q4 + 4], ah[0][3], al[0][3]);
 #pragma unroll
           for (int j = 0; j < 5; ++j) {
-            bf[j][0] = sR[(k0 + q4) * SM_PR + j * 8 + g];
-            bf[j][1] = sR[(k0 + q4 + 4) * SM_PR + j * 8 + g];
+            split_tf32(sR[(k0 + q4) * SM_PR + j * 8 + g], bh[j][0], bl[j][0]);
+            split_tf32(sR[(k0 + q4 + 4) * SM_PR + j * 8 + g], bh[j][1], bl[j][1]);
           }
-#pragma unroll
-          for (int j = 0; j < 5; ++j) mma3(d2[j], af, bf[j]);
+          mma3_tiles<1, 5>(d2, ah, al, bh, bl);
         }
         // stage the output tile in A buffer 0 (free): rows (bi, v, z), cols (v', z')
-        float* st = sAb[0];
+        float* st = sA0;
 #pragma unroll
         for (int j = 0; j < 5; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int m = warp * 16 + g + ((r >> 1) << 3);
             const int n = j * 8 + q4 * 2 + (r & 1);
-            if (m < M2 && n < N2) st[m * SM_PA + n] = d2[j][r];
+            if (m < M2 && n < N2) st[m * SM_PA + n] = d2[0][j][r];
           }
         __syncthreads();
-        // write out: rows over the strided bundle, lanes along the contiguous one
-        if (v_contig) {
-          for (int r = warp; r < nb * nz * nz; r += SM_THREADS / 32) {
-            const int bi = r / (nz * nz), zz = r % (nz * nz), z = zz / nz, zp = zz % nz;
-            const int64_t base = bout[bi] + dv + dz + offZ0[zz];
-            for (int vv = lane; vv < nv * nv; vv += 32) {
-              const int v = vv / nv, vp = vv % nv;
-              out[base + offV0[vv]] = st[(bi * N2 + v * nz + z) * SM_PA + vp * nz + zp];
-            }
-          }
-        } else {
-          for (int r = warp; r < nb * nv * nv; r += SM_THREADS / 32) {
-            const int bi = r / (nv * nv), vv = r % (nv * nv), v = vv / nv, vp = vv % nv;
-            const int64_t base = bout[bi] + dv + dz + offV0[vv];
-            for (int zz = lane; zz < nz * nz; zz += 32) {
-              const int z = zz / nz, zp = zz % nz;
-              out[base + offZ0[zz]] = st[(bi * N2 + v * nz + z) * SM_PA + vp * nz + zp];
-            }
-          }
-        }
+        if (wact)
+          for (int e = w0; e < M2; e += wstep) out[rowOut[e] + obase] = st[e * SM_PA + wcol];
       }
     }
   }
@@ -519,16 +502,22 @@ void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t 
   const int K1 = o.nx * o.ny, N2 = o.nv * o.nz;
   const int nb_per = std::max(1, std::min(144 / K1, 144 / N2));
   const int64_t nblk = nt * nk;
-  const int64_t grid = (nblk + (int64_t)nb_per * SM_GROUPS - 1) / ((int64_t)nb_per * SM_GROUPS);
-  FP_CHECK(grid < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core sandwich: too many blocks");
+  const int64_t ngroups = (nblk + nb_per - 1) / nb_per;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    FP_CUDA(cudaGetDevice(&dev));
+    FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t grid = std::min<int64_t>(ngroups, sms);
   const size_t smem = (size_t)SM_FLOATS * sizeof(float);
   static bool attr = false;
   if (!attr) {
     FP_CUDA(cudaFuncSetAttribute(k_sandwich_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  k_sandwich_mma<<<(unsigned)grid, SM_THREADS, smem, s>>>(o, nt, nk, nb_per, in, i_t, i_k, i_X, i_Y, out, o_t, o_k,
-                                                          o_V, o_Z);
+  k_sandwich_mma<<<(unsigned)grid, SM_THREADS, smem, s>>>(o, nt, nk, nb_per, ngroups, in, i_t, i_k, i_X, i_Y, out,
+                                                          o_t, o_k, o_V, o_Z);
   FP_LAUNCH();
 }
 
