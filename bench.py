@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--probe-theta", type=int, default=0, metavar="NVEC",
+                    help="profiling case: two Theta applications at the central site of the 8x8 chi=500 row "
+                         "with NVEC vectors, then exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -165,9 +168,43 @@ def reduce_ranks(dist, dev, seconds, work):
     return mx[0].item(), sm[1].item()
 
 
+# ----------------------------------------------------------------------------- profiling case
+def theta_probe(nvec: int, prec: str):
+    """Small case for ncu captures: the tensor-core GEMMs and the sandwich of one
+    Theta_c application (central site c = 3 of the 8x8, D=6, chi=500 row), run twice."""
+    import numpy as np
+    import torch
+    from paper_2511_01039_gb300 import fpeps as fp
+    from paper_2511_01039_gb300 import workloads as WL
+    torch.cuda.set_device(0)
+    w = WL.hubbard_row(**WL.C4)
+    env = fp.Env(w.peps, w.pepo, D=w.D, p=w.p, w=w.w, chi=w.chi, prec=prec, seed=1)
+    fp.fpeps_import_boundary(env.h, WL.boundary_blob(w.boundary, w.row, 1, 4), w.row, 1)
+    fp.fpeps_absorb_row(env.h, w.row, 1)
+    c = 3
+    A, W, T = w.peps[w.row][c], w.pepo[w.row][c], w.boundary[c]
+    bundle = [A.shape[i] * W.shape[i] * A.shape[i] for i in range(4)]
+    g = np.random.default_rng(7)
+    el = g.standard_normal((w.chi, T.shape[0], bundle[0])).astype(np.float32)
+    x = g.standard_normal((nvec, T.shape[2], bundle[2])).astype(np.float32)
+    fp.fpeps_profile(True)
+    for _ in range(2):
+        env.apply_theta(c, el, x, bundle[3])
+    for k, name in fp.PROF_KINDS.items():
+        d = fp.fpeps_profile_read(k)
+        if d["launches"]:
+            print(f"{name:16s} launches {d['launches']:4d} {d['ms']:9.2f} ms "
+                  f"{d['flops'] / (d['ms'] * 1e-3) / 1e12:8.2f} TFLOP/s", flush=True)
+    fp.fpeps_profile(False)
+    env.close()
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
+    if args.probe_theta:
+        theta_probe(args.probe_theta, args.prec)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -172,6 +172,9 @@ void permute3(cudaStream_t s, const T* in, T* out, int64_t d0, int64_t d1, int64
 // dst[c * ld_dst + r] = src[r * ld_src + c] for r < rows, c < cols; zero for rows <= r < ld_dst
 template <class T>
 void transpose_pad(cudaStream_t s, const T* src, int64_t rows, int64_t cols, int64_t ld_src, T* dst, int64_t ld_dst);
+// out = a - b elementwise (out may alias a or b)
+template <class T>
+void sub_into(cudaStream_t s, T* out, const T* a, const T* b, int64_t n);
 // dst (col-major rows x cols) = (T) src (row-major rows x cols)
 template <class T>
 void convert_f64_t(cudaStream_t s, const double* src, int64_t rows, int64_t cols, T* dst);

@@ -220,6 +220,47 @@ struct Engine : EngineBase {
     }
     mm(m, n, k, T(1), X, false, ldx, S, false, lds, T(0), out, ldo);
   }
+  // Orthogonal projector onto the complement of the columns of Vm (n x a, col-major,
+  // orthonormal columns). In 3xTF32 mode both products run on the tensor cores:
+  // P = Vm^T X as a K-major product (Vm's columns and X's columns are contiguous),
+  // then Vm P through a K-major copy VmT [n][ap] made once per projector.
+  struct Projector {
+    const T* Vm = nullptr;
+    T* VmT = nullptr;
+    int64_t n = 0;
+    int a = 0, ap = 0;
+    bool tc = false;
+  };
+  Projector projector(Arena& ar, const T* Vm, int64_t n, int a) {
+    Projector P;
+    P.Vm = Vm;
+    P.n = n;
+    P.a = a;
+    P.ap = (a + 3) & ~3;
+    P.tc = sizeof(T) == 4 && mode == FPEPS_TF32X3 && a >= 1 && gemm_tc_supported(a, 1, n, n, n) &&
+           gemm_tc_supported(n, 1, P.ap, P.ap, P.ap) && ((uintptr_t)Vm % 16) == 0;
+    if (P.tc) {
+      P.VmT = ar.get_n<T>((size_t)n * P.ap);
+      transpose_pad<T>(s, Vm, a, n, n, P.VmT, P.ap);
+    }
+    return P;
+  }
+  // out (n x kk, col-major) = X - Vm (Vm^T X); out may alias X; tmp holds a x kk
+  void project_out(const Projector& P, const T* X, T* out, int64_t kk, T* tmp) {
+    if (P.tc && ((uintptr_t)X % 16) == 0) {
+      Arena ar = arena();
+      T* Pm = ar.get_n<T>((size_t)P.ap * kk);
+      if (P.ap != P.a) FP_CUDA(cudaMemsetAsync(Pm, 0, sizeof(T) * P.ap * kk, s));
+      big_gemm(P.a, kk, P.n, P.Vm, P.n, X, P.n, Pm, out_colmajor(P.a, kk, P.ap), false);
+      T* R = ar.get_n<T>((size_t)P.n * kk);
+      big_gemm(P.n, kk, P.ap, P.VmT, P.ap, Pm, P.ap, R, out_colmajor(P.n, kk, P.n), false);
+      sub_into<T>(s, out, X, R, P.n * kk);
+      return;
+    }
+    mm(P.a, kk, P.n, T(1), P.Vm, true, P.n, X, false, P.n, T(0), tmp, P.a);
+    if (out != X) FP_CUDA(cudaMemcpyAsync(out, X, sizeof(T) * P.n * kk, cudaMemcpyDeviceToDevice, s));
+    mm(P.n, kk, P.a, T(-1), P.Vm, false, P.n, tmp, false, P.a, T(1), out, P.n);
+  }
   void mm64(int64_t m, int64_t n, int64_t k, const double* A, bool ta, int64_t lda, const double* B, bool tb,
             int64_t ldb, double* C, int64_t ldc) {
     int64_t am = ta ? lda : 1, ak = ta ? 1 : lda;
@@ -795,15 +836,10 @@ struct Engine : EngineBase {
         T* tmpA = ar.get_n<T>(std::max<int64_t>(a_eff, na) * kmax);
         T* Xp = ar.get_n<T>(std::max(cols_a, rows_a) * kmax);
         T* Zm = ar.get_n<T>(((int64_t)sl.tp * sl.bR) * kmax);
-        auto projR = [&](const T* X, T* out, int64_t kk) {   // out = X - V^T (V X)
-          mm(a_eff, kk, cols_a, T(1), VT, true, cols_a, X, false, cols_a, T(0), tmpA, a_eff);
-          FP_CUDA(cudaMemcpyAsync(out, X, sizeof(T) * cols_a * kk, cudaMemcpyDeviceToDevice, s));
-          mm(cols_a, kk, a_eff, T(-1), VT, false, cols_a, tmpA, false, a_eff, T(1), out, cols_a);
-        };
-        auto projL = [&](T* Y, int64_t kk) {   // Y -= Nl (Nl^T Y)
-          mm(na, kk, rows_a, T(1), Nl, true, rows_a, Y, false, rows_a, T(0), tmpA, na);
-          mm(rows_a, kk, na, T(-1), Nl, false, rows_a, tmpA, false, na, T(1), Y, rows_a);
-        };
+        Projector PR = projector(ar, VT, cols_a, a_eff);
+        Projector PL = projector(ar, Nl, rows_a, na);
+        auto projR = [&](const T* X, T* out, int64_t kk) { project_out(PR, X, out, kk, tmpA); };   // X - V^T (V X)
+        auto projL = [&](T* Y, int64_t kk) { project_out(PL, Y, Y, kk, tmpA); };                 // Y - Nl (Nl^T Y)
         Lin A{rows_a, cols_a,
               [&](const T* X, T* Y, int64_t kk) {
                 projR(X, Xp, kk);
@@ -816,9 +852,7 @@ struct Engine : EngineBase {
                 projL(Xp, kk);
                 theta_t(sl, elc, Xp, Zm, kk);
                 theta_r_t(sc, erc, Zm, X, kk);
-                // X -= V^T (V X)
-                mm(a_eff, kk, cols_a, T(1), VT, true, cols_a, X, false, cols_a, T(0), tmpA, a_eff);
-                mm(cols_a, kk, a_eff, T(-1), VT, false, cols_a, tmpA, false, a_eff, T(1), X, cols_a);
+                project_out(PR, X, X, kk, tmpA);   // X -= V^T (V X)
               }};
         RsvdOut r = rsvd(ar, A, omega, k, prm.power_iters);
         // right singular vectors of numerically zero singular values are not

@@ -1,29 +1,28 @@
-// Split-precision tensor-core GEMM for sm_103a: tcgen05.mma with a TMEM
-// accumulator, operands staged in shared memory by TMA (cp.async.bulk.tensor).
+// Split-precision tensor-core GEMM for sm_103a: tcgen05.mma with TMEM
+// accumulators, operands staged in shared memory by TMA (cp.async.bulk.tensor).
 //
 //   C(m,n) = sum_k A[m][k] B[n][k]      A [M][lda], B [N][ldb] fp32, k contiguous
 //
 // This carries the two chi^2-class contractions of every Fig. 2(a) application
-// (boundary x vectors, environment x vectors). FP32 inputs are split on chip
-// into x = hi + lo and the product is a_hi b_hi + a_hi b_lo + a_lo b_hi with
-// FP32 accumulation in TMEM:
-//   mode 2 (3xTF32): hi = x rounded to TF32 (10-bit mantissa), lo = x - hi
-//                    rounded to TF32 as well (|x - hi - lo| <= 2^-22 |x|),
-//                    kind::tf32 MMAs on the 32-bit tiles.
-// The kernel is persistent (one CTA per SM walks a static tile schedule) with
-// warp roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
-// MMAs (one thread), warps 2-7 split each landed stage into hi/lo tiles (in
-// place + a second buffer; the swizzled layout is preserved element by element),
-// warps 8-11 drain TMEM and store C through the caller's output map.
+// (boundary x vectors, environment x vectors) and the tall-times-small products
+// of the QR and truncation steps. FP32 inputs are split on chip into
+// x = hi + lo, both rounded to TF32 (|x - hi - lo| <= 2^-22 |x|), and the
+// product is a_lo b_hi + a_hi b_lo + a_hi b_hi (kind::tf32 MMAs, "3xTF32").
+//
+// The kernel is persistent (one CTA per SM walks a static tile schedule of
+// 128x128 output tiles, optionally split over K). A's hi/lo tiles live in tensor
+// memory: converter warps read one 128-byte row of the landed fp32 tile per
+// thread and store hi and lo with tcgen05.st, so the MMAs take A from TMEM and
+// only B's hi/lo tiles from shared memory.
 //
 // Accumulation: the tensor cores' FP32 accumulation over long K loses far more
 // than round-to-nearest FP32 (measured ~1e-5 relative at K = 2048, ~1e-3 at
 // K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 256 terms; each
 // chunk accumulates in a fresh TMEM buffer (two buffers, so the MMAs of chunk
-// i+1 overlap the drain of chunk i) and the epilogue warps fold it into a
-// compensated running sum (hi, lo) kept in the other half of TMEM (Knuth's
-// two-sum). Few output tiles are additionally split over K across CTAs, with
-// the partials summed in FP64.
+// i+1 overlap the drain of chunk i) and the epilogue warps add it to a running
+// FP32 sum in TMEM. Few output tiles are additionally split over K across CTAs,
+// with the partials summed in FP64. Output blocks whose contiguous index is n
+// pass through shared memory so that every store instruction is coalesced.
 //
 // Every wait on an mbarrier is bounded: a timeout sets an error word, the CTA
 // stops issuing work, waits (bounded) for what it has in flight, frees its
@@ -39,10 +38,8 @@ namespace fpeps {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32;   // BK fp32 = 128 bytes = one 128B swizzle row
-constexpr int STAGES = 3;
 constexpr int TILE_A = BM * BK * 4, TILE_B = BN * BK * 4;       // bytes
-constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);               // hi + lo of A and B
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;   // tiles + barriers + slack
+constexpr int EPI_TILE = 32 * 33;                                 // floats: one warp's 32x32 output block
 constexpr unsigned long long WAIT_LIMIT = 2000000000ull;   // clock64 cycles (~1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -94,13 +91,6 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
   return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-      : "memory");
-}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -108,21 +98,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 __device__ __forceinline__ uint32_t tf32_round(uint32_t bits) { return (bits + 0x1000u) & 0xFFFFE000u; }
 
-// 32 consecutive TMEM columns of this thread's lane (32x32b shape)
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
 // issue without waiting; tmem_wait32 then waits for every load in flight and
 // ties the registers of one batch to that wait
 __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t* r) {
@@ -173,25 +148,46 @@ struct TcArgs {
   float* part;  // nsplit > 1: partial results [nsplit][M][N] row-major
 };
 
-// Persistent variant: one CTA per SM walks the tiles tile = blockIdx.x + i*gridDim.x.
-// Two TMEM accumulators (2 x BN columns) let the epilogue warps drain tile i
-// while the MMA thread computes tile i+1. Warps: 0 TMA, 1 TMEM + MMA,
-// 2..7 hi/lo converters, 8..11 epilogue (TMEM lane quarters 0..3).
-constexpr int P_THREADS = 384, P_CONV0 = 2, P_NCONV = 6, P_EPI0 = 8;
+// Variant with the A operand in tensor memory. The converter warps of A read one
+// 128-byte row of the landed fp32 tile each (one thread per TMEM lane), split it
+// and store hi and lo straight into a TMEM slot with tcgen05.st; only B's hi/lo
+// tiles stay in shared memory, so the MMAs read B alone from shared memory and the
+// A split costs no shared-memory writes. TMEM columns: [0,256) two chunk
+// accumulators, [256,384) the running FP32 sum, [384,512) two A slots of
+// 32 hi + 32 lo columns. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane
+// quarter = warp % 4), 6..7 B converters, 8..11 epilogue.
+constexpr int P_THREADS = 384;
+constexpr int T_STAGES = 4;
+constexpr int T_STAGE_BYTES = TILE_A + 2 * TILE_B;   // A fp32 | B hi (in place) | B lo
+constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024 + 256 + 4 * EPI_TILE * 4;
+constexpr uint32_t T_RUN = 2 * BN, T_ASLOT = 3 * BN;   // TMEM column bases
+constexpr int T_BCONV0 = 6, T_NBCONV = 2, T_EPI0 = 8;   // warps 2..5 convert A
 
-__global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_constant__ CUtensorMap mapA,
+__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_constant__ CUtensorMap mapA,
                                                                 const __grid_constant__ CUtensorMap mapB, TcArgs g) {
   if (*(volatile int*)g.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* conv = full + STAGES;
-  uint64_t* empty = conv + STAGES;
-  uint64_t* accf = empty + STAGES;
+  uint64_t* full = (uint64_t*)(smem + T_STAGES * T_STAGE_BYTES);
+  uint64_t* bconv = full + T_STAGES;
+  uint64_t* empty = bconv + T_STAGES;
+  uint64_t* aconv = empty + T_STAGES;   // [2] A slot filled
+  uint64_t* aempty = aconv + 2;         // [2] A slot consumed by the MMAs
+  uint64_t* accf = aempty + 2;
   uint64_t* acce = accf + 2;
   uint64_t* drain = acce + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* epi_tiles = (float*)(smem + T_STAGES * T_STAGE_BYTES + 256);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t ntiles = g.mt * g.nt * g.nsplit;
@@ -201,10 +197,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
     kb0 = split * g.ks;
     nk = min(g.ks, nk_all - kb0);
   };
-  auto A_hi = [&](int s) { return smem + s * STAGE_BYTES; };
-  auto B_hi = [&](int s) { return smem + s * STAGE_BYTES + TILE_A; };
-  auto A_lo = [&](int s) { return smem + s * STAGE_BYTES + TILE_A + TILE_B; };
-  auto B_lo = [&](int s) { return smem + s * STAGE_BYTES + 2 * TILE_A + TILE_B; };
+  auto A_f = [&](int st) { return smem + st * T_STAGE_BYTES; };
+  auto B_hi = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A; };
+  auto B_lo = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A + TILE_B; };
   auto tile_mn = [&](int64_t tile, int64_t& m0, int64_t& n0) {
     tile %= g.mt * g.nt;
     const int64_t mt = g.m_fast ? tile % g.mt : tile / g.nt;
@@ -214,12 +209,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
   };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&conv[s], P_NCONV);
-      mbar_init(&empty[s], 1);
+    for (int st = 0; st < T_STAGES; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&bconv[st], T_NBCONV);
+      mbar_init(&empty[st], 1);
     }
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&aconv[b], 4);
+      mbar_init(&aempty[b], 1);
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4);
     }
@@ -250,11 +247,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
         int kb0, nk;
         kslice(tile, kb0, nk);
         for (int kb = 0; kb < nk; ++kb, ++it) {
-          const int s = it % STAGES;
-          if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
-          mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
-          tma_load_2d(A_hi(s), &mapA, &full[s], (kb0 + kb) * BK, (int)m0);
-          tma_load_2d(B_hi(s), &mapB, &full[s], (kb0 + kb) * BK, (int)n0);
+          const int st = it % T_STAGES;
+          if (!mbar_wait(&empty[st], ((it / T_STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
+          mbar_arrive_expect_tx(&full[st], TILE_A + TILE_B);
+          tma_load_2d(A_f(st), &mapA, &full[st], (kb0 + kb) * BK, (int)m0);
+          tma_load_2d(B_hi(st), &mapB, &full[st], (kb0 + kb) * BK, (int)n0);
           ++issued;
         }
       }
@@ -274,61 +271,97 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
           const uint32_t d = tmem + (uint32_t)(buf * BN);
           const int c1 = min(nk, c0 + g.kch);
           for (int kb = c0; kb < c1; ++kb, ++it) {
-            const int s = it % STAGES;
-            if (!mbar_wait(&conv[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+            const int st = it % T_STAGES, as = it & 1;
+            if (!mbar_wait(&bconv[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(&aconv[as], (it >> 1) & 1, abort_flag)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t ah = sdesc(A_hi(s)), bh = sdesc(B_hi(s)), al = sdesc(A_lo(s)), bl = sdesc(B_lo(s));
+            const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
+            const uint32_t ah = tmem + T_ASLOT + (uint32_t)(as * 64), al = ah + 32;
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
               const uint64_t o = (uint64_t)(kk * 32) >> 4;
-              mma_tf32(d, al + o, bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
-              mma_tf32(d, ah + o, bl + o, idesc, 1u);
-              mma_tf32(d, ah + o, bh + o, idesc, 1u);
+              mma_tf32_ts(d, al + (uint32_t)(kk * 8), bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
+              mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
+              mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
             }
-            mma_commit(&empty[s]);
+            mma_commit(&empty[st]);
+            mma_commit(&aempty[as]);
           }
           if (ok) mma_commit(&accf[buf]);
         }
       }
-      // every MMA issued by this thread has completed once `drain` fires
       mma_commit(drain);
       const unsigned long long t0 = clock64();
       while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
       }
     }
-  } else if (warp < P_CONV0 + P_NCONV) {
-    const int cw = warp - P_CONV0;
+  } else if (warp < T_BCONV0) {
+    // A converters: thread = TMEM lane = tile row
+    const int quarter = warp % 4;
+    const int r = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     int it = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int s = it % STAGES;
-        if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
-        uint4* ah = (uint4*)A_hi(s);
-        uint4* bh = (uint4*)B_hi(s);
-        uint4* alo = (uint4*)A_lo(s);
-        uint4* blo = (uint4*)B_lo(s);
-        for (int e = cw * 32 + lane; e < (TILE_A + TILE_B) / 16; e += P_NCONV * 32) {
-          uint4* src = e < TILE_A / 16 ? ah + e : bh + (e - TILE_A / 16);
-          uint4* dlo = e < TILE_A / 16 ? alo + e : blo + (e - TILE_A / 16);
-          uint4 v = *src;
-          uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-          uint4 l = make_uint4(tf32_round(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x))),
-                               tf32_round(__float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y))),
-                               tf32_round(__float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z))),
-                               tf32_round(__float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w))));
-          *src = h;
-          *dlo = l;
+        const int st = it % T_STAGES, as = it & 1;
+        if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&aempty[as], ((it >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint4* row = (const uint4*)(A_f(st) + r * 128);
+        float hi[32], lo[32];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint4 v = row[c ^ (r & 7)];   // 128-byte swizzle: chunk c of row r
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const uint32_t h = tf32_round(w[e]);
+            hi[c * 4 + e] = __uint_as_float(h);
+            lo[c * 4 + e] = __uint_as_float(tf32_round(__float_as_uint(__uint_as_float(w[e]) - __uint_as_float(h))));
+          }
+        }
+        const uint32_t ta = tmem + lane_base + T_ASLOT + (uint32_t)(as * 64);
+        tmem_st32(ta, hi);
+        tmem_st32(ta + 32, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&aconv[as]);
+      }
+    }
+  } else if (warp < T_EPI0) {
+    // B converters: hi in place, lo into the second B tile
+    const int cw = warp - T_BCONV0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int kb0, nk;
+      kslice(tile, kb0, nk);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int st = it % T_STAGES;
+        if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
+        uint4* bh = (uint4*)B_hi(st);
+        uint4* blo = (uint4*)B_lo(st);
+        for (int e = cw * 32 + lane; e < TILE_B / 16; e += T_NBCONV * 32) {
+          const uint4 v = bh[e];
+          const uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+          const uint4 l = make_uint4(tf32_round(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x))),
+                                     tf32_round(__float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y))),
+                                     tf32_round(__float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z))),
+                                     tf32_round(__float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w))));
+          bh[e] = h;
+          blo[e] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&conv[s]);
+        if (lane == 0) mbar_arrive(&bconv[st]);
       }
     }
   } else {
-    const int q = warp - P_EPI0;
+    const int q = warp - T_EPI0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     int lc = 0;
     bool ok = true;
@@ -347,50 +380,50 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
         for (int cb = 0; cb < BN; cb += 32) {
-          float c[32], hi[32], lo[32];
-          uint32_t rc[32], rh[32], rl[32];
+          float v[32];
+          uint32_t rc[32], rr[32];
           tmem_ld32_async(tmem + lane_base + (uint32_t)(buf * BN + cb), rc);
           if (ch == 0) {
             tmem_wait32(rc);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) { c[j] = __uint_as_float(rc[j]); hi[j] = c[j]; lo[j] = 0.f; }
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rc[j]);
           } else {
-            tmem_ld32_async(tmem + lane_base + (uint32_t)(2 * BN + cb), rh);
-            tmem_ld32_async(tmem + lane_base + (uint32_t)(3 * BN + cb), rl);
+            tmem_ld32_async(tmem + lane_base + T_RUN + (uint32_t)cb, rr);
             tmem_wait32(rc);
-            tmem_wait32(rh);
-            tmem_wait32(rl);
+            tmem_wait32(rr);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              c[j] = __uint_as_float(rc[j]);
-              hi[j] = __uint_as_float(rh[j]);
-              lo[j] = __uint_as_float(rl[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {   // two-sum: hi + c = s + e exactly
-              const float sm = hi[j] + c[j];
-              const float bp = sm - hi[j];
-              const float e = (hi[j] - (sm - bp)) + (c[j] - bp);
-              hi[j] = sm;
-              lo[j] += e;
-            }
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]) + __uint_as_float(rc[j]);
           }
           if (ch + 1 < nch) {
-            tmem_st32(tmem + lane_base + (uint32_t)(2 * BN + cb), hi);
-            tmem_st32(tmem + lane_base + (uint32_t)(3 * BN + cb), lo);
-          } else if (mrow && !*abort_flag) {
-            if (g.nsplit > 1) {
-              float* prow = g.part + ((tile / (g.mt * g.nt)) * g.M + m) * g.N;
+            tmem_st32(tmem + lane_base + T_RUN + (uint32_t)cb, v);
+          } else if (!__shfl_sync(0xffffffffu, *abort_flag, 0)) {   // warp-uniform decision
+            if (g.nsplit > 1 || g.om.c3 == 1) {
+              float* tw = epi_tiles + q * EPI_TILE;
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int64_t n = n0 + cb + j;
-                if (n < g.N) prow[n] = hi[j] + lo[j];
+              for (int j = 0; j < 32; ++j) tw[lane * 33 + j] = v[j];
+              __syncwarp();
+              const int64_t n = n0 + cb + lane;
+              const bool ncol = n < g.N;
+              if (g.nsplit > 1) {
+                float* pbase = g.part + (tile / (g.mt * g.nt)) * g.M * g.N + n;
+                for (int r = 0; r < 32; ++r) {
+                  const int64_t mr = m0 + q * 32 + r;
+                  if (mr < g.M && ncol) pbase[mr * g.N] = tw[r * 33 + lane];
+                }
+              } else {
+                const int64_t no = ncol ? (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) : 0;
+                for (int r = 0; r < 32; ++r) {
+                  const int64_t mor = __shfl_sync(0xffffffffu, mo, r);
+                  const int64_t mr = m0 + q * 32 + r;
+                  if (mr < g.M && ncol) g.C[mor + no] = tw[r * 33 + lane];
+                }
               }
-            } else {
+              __syncwarp();
+            } else if (mrow) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const int64_t n = n0 + cb + j;
-                if (n < g.N) g.C[mo + (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) * g.om.c3] = hi[j] + lo[j];
+                if (n < g.N) g.C[mo + (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) * g.om.c3] = v[j];
               }
             }
           }
@@ -404,10 +437,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_p(const __grid_con
   }
 
   if (warp == 0 && lane == 0 && *abort_flag) {
-    for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it) {
-      const int s = it % STAGES;
+    for (int it = issued > T_STAGES ? issued - T_STAGES : 0; it < issued; ++it) {
+      const int st = it % T_STAGES;
       const unsigned long long t0 = clock64();
-      while (!mbar_try_wait(&full[s], (it / STAGES) & 1) && clock64() - t0 < WAIT_LIMIT) {
+      while (!mbar_try_wait(&full[st], (it / T_STAGES) & 1) && clock64() - t0 < WAIT_LIMIT) {
       }
     }
   }
@@ -443,7 +476,7 @@ EncodeTiled encoder() {
   std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = (EncodeTiled)p;
   });
@@ -467,8 +500,9 @@ CUtensorMap make_map(const float* base, int64_t rows, int64_t K, int64_t ld, int
 }  // namespace
 
 bool gemm_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb) {
-  // TMA: 16-byte aligned row strides; tiles must have at least one full box
-  return M >= BM && N >= BN && K >= BK && (lda % 4) == 0 && (ldb % 4) == 0 && lda >= K && ldb >= K &&
+  // TMA: 16-byte aligned row strides, at least one full k-box; rows of a box that
+  // fall outside M or N are filled with zeros and never stored
+  return M >= 1 && N >= 1 && K >= BK && (lda % 4) == 0 && (ldb % 4) == 0 && lda >= K && ldb >= K &&
          M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31);
 }
 
@@ -479,7 +513,7 @@ static int nsplit_of(int64_t tiles, int64_t K, int sms) {
   const int64_t nk = (K + BK - 1) / BK;
   int best = 1;
   double best_eff = 0;
-  for (int sp = 1; sp <= 8; ++sp) {
+  for (int sp = 1; sp <= 64; ++sp) {
     if ((int64_t)sp * KCH_BLOCKS > nk) break;
     const int64_t t = tiles * sp;
     const double eff = (double)t / (double)(((t + sms - 1) / sms) * sms);
@@ -512,7 +546,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
   static bool attr = false;
   if (!attr) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_p, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_BYTES));
     attr = true;
   }
   const int sms = sm_count();
@@ -536,7 +570,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   const int64_t blocks = g.mt * g.nt * g.nsplit;
   FP_CHECK(blocks < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: grid too large");
   ProfToken pt = prof_begin(PROF_GEMM_TC, s, 2.0 * M * N * K, 4.0 * ((double)M * K + (double)N * K + (double)M * N));
-  k_gemm_tf32x3_p<<<(unsigned)std::min<int64_t>(blocks, sms), P_THREADS, SMEM_BYTES, s>>>(ma, mb, g);
+  k_gemm_tf32x3_t<<<(unsigned)std::min<int64_t>(blocks, sms), P_THREADS, T_SMEM_BYTES, s>>>(ma, mb, g);
   FP_LAUNCH();
   if (g.nsplit > 1) {
     const int64_t tot = M * N;

@@ -588,6 +588,12 @@ __global__ void k_convert_f64_t(const double* __restrict__ src, int64_t rows, in
 }
 
 template <class T>
+__global__ void k_sub(T* out, const T* a, const T* b, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a[e] - b[e];
+}
+
+template <class T>
 __global__ void k_permute3(const T* in, T* out, int64_t d0, int64_t d1, int64_t d2, int p0, int p1, int p2) {
   // out dims are (d[p0], d[p1], d[p2]); in is [d0][d1][d2]
   const int64_t n = d0 * d1 * d2;
@@ -818,6 +824,13 @@ void scale_by_inv(cudaStream_t s, T* x, int64_t n, const double* nrm) {
 }
 
 template <class T>
+void sub_into(cudaStream_t s, T* out, const T* a, const T* b, int64_t n) {
+  if (n <= 0) return;
+  k_sub<T><<<grid_for(n), 256, 0, s>>>(out, a, b, n);
+  FP_LAUNCH();
+}
+
+template <class T>
 void transpose_pad(cudaStream_t s, const T* src, int64_t rows, int64_t cols, int64_t ld_src, T* dst, int64_t ld_dst) {
   if (rows <= 0 || cols <= 0) return;
   const int64_t gy = (ld_dst + 31) / 32, gx = (cols + 31) / 32;
@@ -893,6 +906,7 @@ void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst) {
   template void scale_by_inv<T>(cudaStream_t, T*, int64_t, const double*);                                   \
   template void permute3<T>(cudaStream_t, const T*, T*, int64_t, int64_t, int64_t, int, int, int);            \
   template void transpose_pad<T>(cudaStream_t, const T*, int64_t, int64_t, int64_t, T*, int64_t);            \
+  template void sub_into<T>(cudaStream_t, T*, const T*, const T*, int64_t);                                   \
   template void convert_f64_t<T>(cudaStream_t, const double*, int64_t, int64_t, T*);                         \
   template void fill<T>(cudaStream_t, T*, int64_t, T);                                                        \
   template void check_finite<T>(cudaStream_t, const T*, int64_t, int*);                                      \

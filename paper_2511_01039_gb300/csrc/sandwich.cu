@@ -198,7 +198,7 @@ constexpr int SM_MT = 9, SM_PA = 44, SM_PB = 152, SM_PC = 148, SM_PR = 40;
 constexpr int SM_THREADS = 288;   // 9 warps
 constexpr int SM_A = 144 * SM_PA, SM_B = 40 * SM_PB, SM_C = 144 * SM_PC, SM_R = 144 * SM_PR;
 constexpr int SM_TILE_FLOATS = 2 * SM_A + 2 * SM_B + SM_C + SM_R;
-constexpr int SM_FLOATS = SM_TILE_FLOATS + 2 * (144 + 144) + 144;   // + int64 row tables, int32 A offsets
+constexpr int SM_FLOATS = SM_TILE_FLOATS + 2 * (144 + 144) + 144 + 2 * 144;   // + row tables, A / C offsets
 
 // round to the nearest TF32 value, ties away from zero, with integer operations
 // on the bit pattern (sign-magnitude: adding half an ulp to the magnitude)
@@ -267,6 +267,8 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
   int64_t* const rowIn = reinterpret_cast<int64_t*>(sR + SM_R);   // [blk][x y] input offset
   int64_t* const rowOut = rowIn + 144;                            // [blk][v z] output offset
   int* const dstA = reinterpret_cast<int*>(rowOut + 144);         // [blk][x y] A-tile offset
+  int* const cRow = dstA + 144;   // sC offset of ket accumulator row m = (blk, x', y')
+  int* const cCol = cRow + 144;   // sC offset of ket accumulator column n = (v, z, q)
   const float* AW = static_cast<const float*>(o.d_aw);
   const float* AR = static_cast<const float*>(o.d_ar);
   const int nx = o.nx, ny = o.ny, nv = o.nv, nz = o.nz, p = o.p;
@@ -295,6 +297,11 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
 
   for (int e = tid; e < SM_TILE_FLOATS; e += SM_THREADS) sm[e] = 0.f;
   __syncthreads();
+  // sC[(blk N2 + vz) SM_PC + xy p + q] = cRow[m] + cCol[n] for m = (blk, xy), n = (vz, q)
+  for (int e = tid; e < 144; e += SM_THREADS) {
+    cRow[e] = (e / K1) * N2 * SM_PC + (e % K1) * p;
+    cCol[e] = (e / p) * SM_PC + e % p;
+  }
   for (int e = tid; e < K2 * N2; e += SM_THREADS) {
     int r = e / N2, c = e % N2;            // r = (x', y', q), c = (v', z')
     int q = r % p, xy = r / p, yp = xy % ny, xp = xy / ny;
@@ -403,32 +410,44 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
             for (int r = 0; r < 4; ++r) {
               const int m = (mg * 3 + i) * 16 + g + ((r >> 1) << 3);
               const int n = (ng * 6 + j) * 8 + q4 * 2 + (r & 1);
-              if (m < M1 && n < N1) {
-                int bi = m / K1, xy = m % K1;
-                int q = n % p, vz = n / p;
-                sC[(bi * N2 + vz) * SM_PC + xy * p + q] = acc[i][j][r];
-              }
+              if (m < M1 && n < N1) sC[cRow[m] + cCol[n]] = acc[i][j][r];
             }
         __syncthreads();
         // bra: rows (bi, v, z) x cols (v', z'), K = (x', y', q)
-        float d2[1][5][4];
+        // two accumulator sets over alternating k-steps: 10 independent MMA chains
+        float d2[2][5][4];
 #pragma unroll
-        for (int j = 0; j < 5; ++j)
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) d2[0][j][r] = 0.f;
-        for (int k0 = 0; k0 < K2p; k0 += 8) {
-          uint32_t ah[1][4], al[1][4], bh[5][2], bl[5][2];
-          const int r0 = warp * 16 + g;
-          split_tf32(sC[r0 * SM_PC + k0 + q4], ah[0][0], al[0][0]);
-          split_tf32(sC[(r0 + 8) * SM_PC + k0 + q4], ah[0][1], al[0][1]);
-          split_tf32(sC[r0 * SM_PC + k0 + q4 + 4], ah[0][2], al[0][2]);
-          split_tf32(sC[(r0 + 8) * SM_PC + k0 + q4 + 4], ah[0][3], al[0][3]);
+          for (int j = 0; j < 5; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) d2[u][j][r] = 0.f;
+        const int r0 = warp * 16 + g;
+        auto bra_step = [&](int kk, uint32_t(&ah)[1][4], uint32_t(&al)[1][4], uint32_t(&bh)[5][2],
+                            uint32_t(&bl)[5][2]) {
+          split_tf32(sC[r0 * SM_PC + kk + q4], ah[0][0], al[0][0]);
+          split_tf32(sC[(r0 + 8) * SM_PC + kk + q4], ah[0][1], al[0][1]);
+          split_tf32(sC[r0 * SM_PC + kk + q4 + 4], ah[0][2], al[0][2]);
+          split_tf32(sC[(r0 + 8) * SM_PC + kk + q4 + 4], ah[0][3], al[0][3]);
 #pragma unroll
           for (int j = 0; j < 5; ++j) {
-            split_tf32(sR[(k0 + q4) * SM_PR + j * 8 + g], bh[j][0], bl[j][0]);
-            split_tf32(sR[(k0 + q4 + 4) * SM_PR + j * 8 + g], bh[j][1], bl[j][1]);
+            split_tf32(sR[(kk + q4) * SM_PR + j * 8 + g], bh[j][0], bl[j][0]);
+            split_tf32(sR[(kk + q4 + 4) * SM_PR + j * 8 + g], bh[j][1], bl[j][1]);
           }
-          mma3_tiles<1, 5>(d2, ah, al, bh, bl);
+        };
+        int k0 = 0;
+        for (; k0 + 16 <= K2p; k0 += 16) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            uint32_t ah0[1][4], al0[1][4], bh0[5][2], bl0[5][2];
+            bra_step(k0 + 8 * u, ah0, al0, bh0, bl0);
+            mma3_tiles<1, 5>(&d2[u], ah0, al0, bh0, bl0);
+          }
+        }
+        if (k0 < K2p) {   // K2p / 8 odd: one k-step left
+          uint32_t ah0[1][4], al0[1][4], bh0[5][2], bl0[5][2];
+          bra_step(k0, ah0, al0, bh0, bl0);
+          mma3_tiles<1, 5>(&d2[0], ah0, al0, bh0, bl0);
         }
         // stage the output tile in A buffer 0 (free): rows (bi, v, z), cols (v', z')
         float* st = sA0;
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
           for (int r = 0; r < 4; ++r) {
             const int m = warp * 16 + g + ((r >> 1) << 3);
             const int n = j * 8 + q4 * 2 + (r & 1);
-            if (m < M2 && n < N2) st[m * SM_PA + n] = d2[0][j][r];
+            if (m < M2 && n < N2) st[m * SM_PA + n] = d2[0][j][r] + d2[1][j][r];
           }
         __syncthreads();
         if (wact)

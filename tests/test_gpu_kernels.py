@@ -17,7 +17,8 @@ def fp():
 
 @pytest.mark.parametrize("M,N,K,pad", [(300, 260, 100, 0), (128, 128, 32, 0), (1000, 2000, 512, 4),
                                        (4100, 700, 1000, 12), (130, 4097, 36, 0), (500, 432, 108000, 0),
-                                       (260, 300, 4100, 8)])
+                                       (260, 300, 4100, 8), (500, 60, 108000, 0), (64, 256, 1000, 0),
+                                       (1, 9, 40, 0), (3000, 7, 500, 4)])
 @pytest.mark.parametrize("mode", ["tf32x3", "f32"])
 def test_gemm_against_fp64(fp, M, N, K, pad, mode):
     import torch
@@ -40,13 +41,15 @@ def test_gemm_against_fp64(fp, M, N, K, pad, mode):
 
 
 def test_gemm_tc_rejects_unsupported_shapes(fp):
+    """K below one 32-wide k-box, or rows not 16-byte aligned (TMA strides)."""
     import torch
-    A = torch.randn(64, 32, device="cuda")
-    B = torch.randn(256, 32, device="cuda")
-    C = torch.empty(64, 256, device="cuda")
-    with pytest.raises(fp.FpepsError) as ei:
-        fp.fpeps_gemm_f32(fp.TF32X3, A, B, C)
-    assert ei.value.status == 7
+    for K, ld in [(16, 16), (34, 34)]:
+        A = torch.randn(64, ld, device="cuda")
+        B = torch.randn(256, ld, device="cuda")
+        C = torch.empty(64, 256, device="cuda")
+        with pytest.raises(fp.FpepsError) as ei:
+            fp.fpeps_gemm_f32(fp.TF32X3, A, B, C, K=K)
+        assert ei.value.status == 7
 
 
 @pytest.mark.parametrize("k", [7, 64, 200, 511])
