@@ -318,13 +318,21 @@ def main():
     hbm = peaks.get("hbm_gbs", 6800.0)
     src = "of measured" if peaks else "of fallback"
     d = prof[dom]
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of
+    # the kernel, from one ncu capture of the probe case (bench.py --probe-theta 8:
+    # both GEMM launches, one sandwich launch); traffic per launch = ratio x the
+    # algorithmic bytes of an average launch here (traffic grows with the bytes moved)
+    dram_per_alg_byte = {"gemm_tc_tf32x3": (0.911 + 1.021) / (2 * 0.966), "sandwich": 3.263 / 1.493}
+    traffic = None
+    if dom in dram_per_alg_byte and d["launches"]:
+        traffic = dram_per_alg_byte[dom] * d["bytes"] / d["launches"]
     tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if args.prec == "tf32x3" else ("gemm_tc_tf32x3",)
     if dom in tensor_kinds:
         # TF32 dense peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1/2.25)
         peak = bf16 * 1.1 / 2.25
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "note": f"TF32 peak = {src} BF16 x 1.1/2.25; algorithmic flops, and 3xTF32 issues 3 MMAs per "
                         f"product, so frac <= 1/3"}
     elif dom in ("gemm_simt", "sandwich"):
