@@ -145,6 +145,7 @@ struct TcArgs {
   int ks;       // k-blocks per K slice (split-K); nsplit = ceil(nk / ks)
   int nsplit;
   int kch;      // k-blocks per TMEM accumulation chunk
+  int naslot;   // TMEM A slots: 4 when every tile is one chunk (no running sum), else 2
   float* part;  // nsplit > 1: partial results [nsplit][M][N] row-major
 };
 
@@ -180,9 +181,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   uint64_t* full = (uint64_t*)(smem + T_STAGES * T_STAGE_BYTES);
   uint64_t* bconv = full + T_STAGES;
   uint64_t* empty = bconv + T_STAGES;
-  uint64_t* aconv = empty + T_STAGES;   // [2] A slot filled
-  uint64_t* aempty = aconv + 2;         // [2] A slot consumed by the MMAs
-  uint64_t* accf = aempty + 2;
+  uint64_t* aconv = empty + T_STAGES;   // [4] A slot filled
+  uint64_t* aempty = aconv + 4;         // [4] A slot consumed by the MMAs
+  uint64_t* accf = aempty + 4;
   uint64_t* acce = accf + 2;
   uint64_t* drain = acce + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
@@ -214,9 +215,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       mbar_init(&bconv[st], T_NBCONV);
       mbar_init(&empty[st], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
       mbar_init(&aconv[b], 4);
       mbar_init(&aempty[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4);
     }
@@ -233,6 +236,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // A slots: columns [384, 512) (two), or [256, 512) (four) when no running sum is kept
+  const uint32_t abase = g.naslot == 4 ? T_RUN : T_ASLOT;
 
   int issued = 0;
   if (warp == 0) {
@@ -271,12 +276,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
           const uint32_t d = tmem + (uint32_t)(buf * BN);
           const int c1 = min(nk, c0 + g.kch);
           for (int kb = c0; kb < c1; ++kb, ++it) {
-            const int st = it % T_STAGES, as = it & 1;
+            const int st = it % T_STAGES, as = it % g.naslot;
             if (!mbar_wait(&bconv[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-            if (!mbar_wait(&aconv[as], (it >> 1) & 1, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(&aconv[as], (it / g.naslot) & 1, abort_flag)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
-            const uint32_t ah = tmem + T_ASLOT + (uint32_t)(as * 64), al = ah + 32;
+            const uint32_t ah = tmem + abase + (uint32_t)(as * 64), al = ah + 32;
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
               const uint64_t o = (uint64_t)(kk * 32) >> 4;
@@ -306,9 +311,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int st = it % T_STAGES, as = it & 1;
+        const int st = it % T_STAGES, as = it % g.naslot;
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-        if (!mbar_wait(&aempty[as], ((it >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&aempty[as], ((it / g.naslot) & 1) ^ 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint4* row = (const uint4*)(A_f(st) + r * 128);
         float hi[32], lo[32];
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             lo[c * 4 + e] = __uint_as_float(tf32_round(__float_as_uint(__uint_as_float(w[e]) - __uint_as_float(h))));
           }
         }
-        const uint32_t ta = tmem + lane_base + T_ASLOT + (uint32_t)(as * 64);
+        const uint32_t ta = tmem + lane_base + abase + (uint32_t)(as * 64);
         tmem_st32(ta, hi);
         tmem_st32(ta + 32, lo);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -562,6 +567,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   g.ks = (int)((nk + g.nsplit - 1) / g.nsplit);
   g.nsplit = (int)((nk + g.ks - 1) / g.ks);   // every slice non-empty
   g.kch = g.ks <= 2 * KCH_BLOCKS ? g.ks : KCH_BLOCKS;
+  g.naslot = (g.ks + g.kch - 1) / g.kch == 1 ? 4 : 2;
   g.part = nullptr;
   if (g.nsplit > 1) {
     FP_CHECK(scratch_bytes >= gemm_tc_scratch_bytes(mode, M, N, K), FPEPS_ERR_ARG, "tensor-core GEMM: scratch too small");

@@ -349,8 +349,12 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
       }
     };
 
-    for (int vw = 0; vw < o.nvw; ++vw) {
-      for (int zw = 0; zw < o.nzw; ++zw) {
+    // output pairs with the contiguous bundle's channel index innermost, so that
+    // consecutive pairs store adjacent bundle runs while they are still in L2
+    const int nouter = v_fast ? o.nzw : o.nvw, ninner = v_fast ? o.nvw : o.nzw;
+    for (int po = 0; po < nouter; ++po) {
+      for (int pi = 0; pi < ninner; ++pi) {
+        const int vw = v_fast ? pi : po, zw = v_fast ? po : pi;
         const int pair = vw * o.nzw + zw;
         const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
         const int64_t obase = (int64_t)vw * nv * o_V + (int64_t)zw * nz * o_Z + wpart;
