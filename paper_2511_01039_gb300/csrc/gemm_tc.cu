@@ -155,14 +155,16 @@ struct TcArgs {
 // tiles stay in shared memory, so the MMAs read B alone from shared memory and the
 // A split costs no shared-memory writes. TMEM columns: [0,256) two chunk
 // accumulators, [256,384) the running FP32 sum, [384,512) two A slots of
-// 32 hi + 32 lo columns. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane
-// quarter = warp % 4), 6..7 B converters, 8..11 epilogue.
-constexpr int P_THREADS = 384;
+// 32 hi + 32 lo columns (four slots from column 256 when no running sum is
+// kept). Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane quarter =
+// warp % 4), 6..7 and 12..15 B converters, 8..11 epilogue.
+constexpr int P_THREADS = 512;
 constexpr int T_STAGES = 4;
 constexpr int T_STAGE_BYTES = TILE_A + 2 * TILE_B;   // A fp32 | B hi (in place) | B lo
 constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024 + 256 + 4 * EPI_TILE * 4;
 constexpr uint32_t T_RUN = 2 * BN, T_ASLOT = 3 * BN;   // TMEM column bases
-constexpr int T_BCONV0 = 6, T_NBCONV = 2, T_EPI0 = 8;   // warps 2..5 convert A
+// warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue
+constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12;
 
 __device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
                                             uint32_t acc) {
@@ -337,9 +339,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         if (lane == 0) mbar_arrive(&aconv[as]);
       }
     }
-  } else if (warp < T_EPI0) {
+  } else if (warp < T_EPI0 || warp >= T_BCONV1) {
     // B converters: hi in place, lo into the second B tile
-    const int cw = warp - T_BCONV0;
+    const int cw = warp < T_EPI0 ? warp - T_BCONV0 : warp - T_BCONV1 + (T_EPI0 - T_BCONV0);
     int it = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -350,6 +352,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
         uint4* bh = (uint4*)B_hi(st);
         uint4* blo = (uint4*)B_lo(st);
+#pragma unroll 3
         for (int e = cw * 32 + lane; e < TILE_B / 16; e += T_NBCONV * 32) {
           const uint4 v = bh[e];
           const uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));

@@ -462,12 +462,20 @@ __global__ void __launch_bounds__(256) k_jacobi_svd_coop(double* M, double* V, i
   double* fro2p = (double*)&ws[2];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x)
     V[e] = ((e / k) == (e % k)) ? 1.0 : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0) {   // ||M||_F^2 by block 0
+    __shared__ double red[32];
     double f = 0;
-    for (int64_t e = 0; e < (int64_t)k * k; ++e) f = fma(M[e], M[e], f);
-    *fro2p = f;
-    ws[0] = 0;
-    ws[1] = 0;
+    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) f = fma(M[e], M[e], f);
+    for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) red[threadIdx.x / 32] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+      *fro2p = t;
+      ws[0] = 0;
+      ws[1] = 0;
+    }
   }
   grid.sync();
   const double tiny = 1e-30 * (*fro2p);
@@ -770,11 +778,13 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
       int dev = 0, sms = 0, per = 0;
       FP_CUDA(cudaGetDevice(&dev));
       FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0));
+      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 64, 0));
       max_blocks[ti] = sms * std::max(per, 0);
     }
     int pairs = (k + 1) / 2;
-    int blocks = std::min(max_blocks[ti], (pairs + 7) / 8);
+    // FP64 runs at ~4 flop/cycle per SM here, so a rotation (~12k flop) is compute-
+    // bound on one SM: two warps per block spread the pairs of a round over the SMs
+    int blocks = std::min(max_blocks[ti], (pairs + 1) / 2);
     FP_CHECK(blocks >= 1, FPEPS_ERR_CUDA, "svd: no co-resident blocks");
     unsigned long long* ws = (unsigned long long*)ws_dev;
     int max_sweeps = 30;
@@ -782,7 +792,7 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
     void* args[] = {&Mat, &V, &k, &max_sweeps, &eps, &ws};
     ProfToken pt = prof_begin(PROF_FACTOR, s, 0.0, 16.0 * k * k);
     count_launch();
-    FP_CUDA(cudaLaunchCooperativeKernel(fn, blocks, 256, args, 0, s));
+    FP_CUDA(cudaLaunchCooperativeKernel(fn, blocks, 64, args, 0, s));
     prof_end(pt, s);
     FP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
     static const bool trace = getenv("FPEPS_TRACE_SVD") != nullptr;   // diagnostics: sweeps used
