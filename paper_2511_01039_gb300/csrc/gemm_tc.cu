@@ -157,14 +157,28 @@ struct TcArgs {
 // accumulators, [256,384) the running FP32 sum, [384,512) two A slots of
 // 32 hi + 32 lo columns (four slots from column 256 when no running sum is
 // kept). Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane quarter =
-// warp % 4), 6..7 and 12..15 B converters, 8..11 epilogue.
-constexpr int P_THREADS = 512;
+// warp % 4), 6..7 and 12..15 B converters, 8..11 epilogue, 16 barrier waiter
+// for the MMA warp.
+constexpr int P_THREADS = 544;
 constexpr int T_STAGES = 4;
 constexpr int T_STAGE_BYTES = TILE_A + 2 * TILE_B;   // A fp32 | B hi (in place) | B lo
 constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024 + 256 + 4 * EPI_TILE * 4;
 constexpr uint32_t T_RUN = 2 * BN, T_ASLOT = 3 * BN;   // TMEM column bases
-// warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue
-constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12;
+// warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue,
+// 16 waiter
+constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12, T_WAITER = 16;
+
+// named barrier 1 between the MMA warp and the waiter warp (64 threads); returns
+// true if any participating thread passed true
+__device__ __forceinline__ bool handoff_abort(bool mine) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 64, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)mine)
+      : "memory");
+  return r != 0;
+}
 
 __device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
                                             uint32_t acc) {
@@ -264,24 +278,26 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-      int it = 0, lc = 0;
-      bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int kb0, nk;
-        kslice(tile, kb0, nk);
-        for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
-          const int buf = lc & 1;
-          if (!mbar_wait(&acce[buf], ((lc >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+    // The MMA warp touches no shared memory while MMAs are in flight: an mbarrier
+    // wait by the thread that issued tcgen05.mma stalls it until those MMAs have
+    // drained (measured: one wait per 12 MMAs halves the tensor-pipe rate). The
+    // waiter warp does the mbarrier waits and hands each ready k-block over on a
+    // named barrier, whose OR-reduction also carries an abort.
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    int it = 0, lc = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int kb0, nk;
+      kslice(tile, kb0, nk);
+      for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
+        const int buf = lc & 1;
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        const int c1 = min(nk, c0 + g.kch);
+        for (int kb = c0; kb < c1; ++kb, ++it) {
+          if (handoff_abort(false)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t d = tmem + (uint32_t)(buf * BN);
-          const int c1 = min(nk, c0 + g.kch);
-          for (int kb = c0; kb < c1; ++kb, ++it) {
-            const int st = it % T_STAGES, as = it % g.naslot;
-            if (!mbar_wait(&bconv[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-            if (!mbar_wait(&aconv[as], (it / g.naslot) & 1, abort_flag)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int st = it % T_STAGES, as = it % g.naslot;
+          if (lane == 0) {
             const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
             const uint32_t ah = tmem + abase + (uint32_t)(as * 64), al = ah + 32;
 #pragma unroll
@@ -293,13 +309,42 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             }
             mma_commit(&empty[st]);
             mma_commit(&aempty[as]);
+            if (kb + 1 == c1) mma_commit(&accf[buf]);
           }
-          if (ok) mma_commit(&accf[buf]);
+          __syncwarp();
         }
       }
+    }
+    if (lane == 0) {
       mma_commit(drain);
       const unsigned long long t0 = clock64();
       while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
+      }
+    }
+    __syncwarp();
+  } else if (warp == T_WAITER) {
+    // waits for the inputs of every k-block (and, at a chunk start, for the
+    // accumulator buffer) in the MMA warp's order, then hands the k-block over
+    int it = 0, lc = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int kb0, nk;
+      kslice(tile, kb0, nk);
+      for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
+        const int buf = lc & 1;
+        const int c1 = min(nk, c0 + g.kch);
+        for (int kb = c0; kb < c1; ++kb, ++it) {
+          const int st = it % T_STAGES, as = it % g.naslot;
+          bool ready = true;
+          if (kb == c0) ready = mbar_wait(&acce[buf], ((lc >> 1) & 1) ^ 1, abort_flag);
+          ready = ready && mbar_wait(&bconv[st], (it / T_STAGES) & 1, abort_flag);
+          ready = ready && mbar_wait(&aconv[as], (it / g.naslot) & 1, abort_flag);
+          // relay the converters' tensor-memory stores to the MMA warp
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          const bool any_abort = handoff_abort(!__all_sync(0xffffffffu, ready));
+          if (any_abort) { ok = false; break; }
+        }
       }
     }
   } else if (warp < T_BCONV0) {
@@ -339,7 +384,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         if (lane == 0) mbar_arrive(&aconv[as]);
       }
     }
-  } else if (warp < T_EPI0 || warp >= T_BCONV1) {
+  } else if (warp < T_EPI0 || (warp >= T_BCONV1 && warp < T_WAITER)) {
     // B converters: hi in place, lo into the second B tile
     const int cw = warp < T_EPI0 ? warp - T_BCONV0 : warp - T_BCONV1 + (T_EPI0 - T_BCONV0);
     int it = 0;
@@ -444,16 +489,21 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     }
   }
 
-  if (warp == 0 && lane == 0 && *abort_flag) {
-    for (int it = issued > T_STAGES ? issued - T_STAGES : 0; it < issued; ++it) {
-      const int st = it % T_STAGES;
-      const unsigned long long t0 = clock64();
-      while (!mbar_try_wait(&full[st], (it / T_STAGES) & 1) && clock64() - t0 < WAIT_LIMIT) {
+  // every role has left its loop (finished or aborted) once all threads meet here;
+  // only then is the abort flag final
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort_flag) {
+    if (warp == 0 && lane == 0) {   // wait (bounded) for the TMA loads still in flight
+      for (int it = issued > T_STAGES ? issued - T_STAGES : 0; it < issued; ++it) {
+        const int st = it % T_STAGES;
+        const unsigned long long t0 = clock64();
+        while (!mbar_try_wait(&full[st], (it / T_STAGES) & 1) && clock64() - t0 < WAIT_LIMIT) {
+        }
       }
     }
+    if (threadIdx.x == 0) atomicExch(g.err, 1);
   }
-  if (threadIdx.x == 0 && *abort_flag) atomicExch(g.err, 1);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
