@@ -307,8 +307,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
               mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
               mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
             }
-            mma_commit(&empty[st]);
-            mma_commit(&aempty[as]);
+            mma_commit(&empty[st]);   // with four A slots, also frees A slot as == st
+            if (g.naslot != T_STAGES) mma_commit(&aempty[as]);
             if (kb + 1 == c1) mma_commit(&accf[buf]);
           }
           __syncwarp();
@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int st = it % T_STAGES, as = it % g.naslot;
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-        if (!mbar_wait(&aempty[as], ((it / g.naslot) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        uint64_t* slot_free = g.naslot == T_STAGES ? &empty[st] : &aempty[as];   // same ring when 4 slots
+        if (!mbar_wait(slot_free, ((it / g.naslot) & 1) ^ 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint4* row = (const uint4*)(A_f(st) + r * 128);
         float hi[32], lo[32];
