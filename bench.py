@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--full-sweep", action="store_true",
+                    help="time one full <psi|H|psi> / <psi|psi> evaluation of the 8x8 lattice (every row "
+                         "absorbed and compressed, both layers) and print one JSON line, then exit")
     ap.add_argument("--probe-theta", type=int, default=0, metavar="NVEC",
                     help="profiling case: two Theta applications at the central site of the 8x8 chi=500 row "
                          "with NVEC vectors, then exit (no JSON line)")
@@ -199,11 +202,36 @@ def theta_probe(nvec: int, prec: str):
     env.close()
 
 
+def full_sweep(prec: str):
+    """<H> = <psi|H|psi> / <psi|psi> of the 8x8, D=6, w=6, chi=500 lattice: two top-to-bottom
+    boundary sweeps (operator layer and norm layer), every interior row compressed by zip-up
+    rSVD + one CBE fit pass."""
+    import torch
+    from paper_2511_01039_gb300 import fpeps as fp
+    from paper_2511_01039_gb300 import workloads as WL
+    torch.cuda.set_device(0)
+    w = WL.hubbard_row(**WL.C4)
+    env = fp.Env(w.peps, w.pepo, D=w.D, p=w.p, w=w.w, chi=w.chi, prec=prec, seed=1)
+    prm = fp.params(oversample=10, power_iters=2, chi_tilde=0, n_fit=1, exact_svd=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    val, sn, ln = env.expect(prm)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    env.close()
+    print(json.dumps({"workload": "8x8 PEPS D=6 p=4, Hubbard-shaped FSM PEPO w=6, chi=500: <psi|H|psi> and "
+                                  "<psi|psi> by full boundary sweeps", "precision": prec, "seconds": el,
+                      "energy": val, "num_sign": sn, "num_log": ln}), flush=True)
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
     if args.probe_theta:
         theta_probe(args.probe_theta, args.prec)
+        return
+    if args.full_sweep:
+        full_sweep(args.prec)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
