@@ -18,10 +18,11 @@
 // Accumulation: the tensor cores' FP32 accumulation over long K loses far more
 // than round-to-nearest FP32 (measured ~1e-5 relative at K = 2048, ~1e-3 at
 // K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 256 terms; each
-// chunk accumulates in a fresh TMEM buffer (two buffers, so the MMAs of chunk
-// i+1 overlap the drain of chunk i) and the epilogue warps add it to a running
-// FP32 sum in TMEM. Few output tiles are additionally split over K across CTAs,
-// with the partials summed in FP64. Output blocks whose contiguous index is n
+// chunk accumulates in a fresh TMEM accumulator and the epilogue warps add it to
+// a running FP32 sum in TMEM (the MMAs of the next chunk wait for that drain;
+// tiles of a single chunk alternate two accumulators instead, so a tile's MMAs
+// overlap the previous tile's drain). Few output tiles are additionally split
+// over K across CTAs, with the partials summed in FP64. Output blocks whose contiguous index is n
 // pass through shared memory so that every store instruction is coalesced.
 //
 // Every wait on an mbarrier is bounded: a timeout sets an error word, the CTA
@@ -145,7 +146,7 @@ struct TcArgs {
   int ks;       // k-blocks per K slice (split-K); nsplit = ceil(nk / ks)
   int nsplit;
   int kch;      // k-blocks per TMEM accumulation chunk
-  int naslot;   // TMEM A slots: 4 when every tile is one chunk (no running sum), else 2
+  int nbuf;     // TMEM chunk accumulators: 2 when every tile is one chunk, else 1 (+ running sum)
   float* part;  // nsplit > 1: partial results [nsplit][M][N] row-major
 };
 
@@ -153,17 +154,17 @@ struct TcArgs {
 // 128-byte row of the landed fp32 tile each (one thread per TMEM lane), split it
 // and store hi and lo straight into a TMEM slot with tcgen05.st; only B's hi/lo
 // tiles stay in shared memory, so the MMAs read B alone from shared memory and the
-// A split costs no shared-memory writes. TMEM columns: [0,256) two chunk
-// accumulators, [256,384) the running FP32 sum, [384,512) two A slots of
-// 32 hi + 32 lo columns (four slots from column 256 when no running sum is
-// kept). Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane quarter =
+// A split costs no shared-memory writes. TMEM columns: [0,128) a chunk
+// accumulator; [128,256) a second one when every tile is a single chunk (tiles
+// alternate, so the next tile's MMAs overlap the drain), else the running FP32
+// sum; [256,512) four A slots of 32 hi + 32 lo columns, one per stage. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane quarter =
 // warp % 4), 6..7 and 12..15 B converters, 8..11 epilogue, 16 barrier waiter
 // for the MMA warp.
 constexpr int P_THREADS = 544;
 constexpr int T_STAGES = 4;
 constexpr int T_STAGE_BYTES = TILE_A + 2 * TILE_B;   // A fp32 | B hi (in place) | B lo
 constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024 + 256 + 4 * EPI_TILE * 4;
-constexpr uint32_t T_RUN = 2 * BN, T_ASLOT = 3 * BN;   // TMEM column bases
+constexpr uint32_t T_RUN = BN, T_ASLOT = 2 * BN;   // TMEM column bases (see the layout above)
 // warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue,
 // 16 waiter
 constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12, T_WAITER = 16;
@@ -197,9 +198,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   uint64_t* full = (uint64_t*)(smem + T_STAGES * T_STAGE_BYTES);
   uint64_t* bconv = full + T_STAGES;
   uint64_t* empty = bconv + T_STAGES;
-  uint64_t* aconv = empty + T_STAGES;   // [4] A slot filled
-  uint64_t* aempty = aconv + 4;         // [4] A slot consumed by the MMAs
-  uint64_t* accf = aempty + 4;
+  uint64_t* aconv = empty + T_STAGES;   // [4] A slot filled (A slot = stage index; freed with the stage)
+  uint64_t* accf = aconv + 4;
   uint64_t* acce = accf + 2;
   uint64_t* drain = acce + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
@@ -231,10 +231,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       mbar_init(&bconv[st], T_NBCONV);
       mbar_init(&empty[st], 1);
     }
-    for (int b = 0; b < 4; ++b) {
-      mbar_init(&aconv[b], 4);
-      mbar_init(&aempty[b], 1);
-    }
+    for (int b = 0; b < 4; ++b) mbar_init(&aconv[b], 4);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4);
@@ -252,8 +249,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  // A slots: columns [384, 512) (two), or [256, 512) (four) when no running sum is kept
-  const uint32_t abase = g.naslot == 4 ? T_RUN : T_ASLOT;
+  // A slots: columns [256, 512), one per stage
+  const uint32_t abase = T_ASLOT;
 
   int issued = 0;
   if (warp == 0) {
@@ -290,13 +287,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
-        const int buf = lc & 1;
+        const int buf = lc % g.nbuf;
         const uint32_t d = tmem + (uint32_t)(buf * BN);
         const int c1 = min(nk, c0 + g.kch);
         for (int kb = c0; kb < c1; ++kb, ++it) {
           if (handoff_abort(false)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int st = it % T_STAGES, as = it % g.naslot;
+          const int st = it % T_STAGES, as = st;
           if (lane == 0) {
             const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
             const uint32_t ah = tmem + abase + (uint32_t)(as * 64), al = ah + 32;
@@ -307,8 +304,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
               mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
               mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
             }
-            mma_commit(&empty[st]);   // with four A slots, also frees A slot as == st
-            if (g.naslot != T_STAGES) mma_commit(&aempty[as]);
+            mma_commit(&empty[st]);   // frees the stage and its A slot
             if (kb + 1 == c1) mma_commit(&accf[buf]);
           }
           __syncwarp();
@@ -331,14 +327,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
-        const int buf = lc & 1;
+        const int buf = lc % g.nbuf;
         const int c1 = min(nk, c0 + g.kch);
         for (int kb = c0; kb < c1; ++kb, ++it) {
-          const int st = it % T_STAGES, as = it % g.naslot;
+          const int st = it % T_STAGES, as = st;
           bool ready = true;
-          if (kb == c0) ready = mbar_wait(&acce[buf], ((lc >> 1) & 1) ^ 1, abort_flag);
+          if (kb == c0) ready = mbar_wait(&acce[buf], ((lc / g.nbuf) & 1) ^ 1, abort_flag);
           ready = ready && mbar_wait(&bconv[st], (it / T_STAGES) & 1, abort_flag);
-          ready = ready && mbar_wait(&aconv[as], (it / g.naslot) & 1, abort_flag);
+          ready = ready && mbar_wait(&aconv[as], (it / T_STAGES) & 1, abort_flag);
           // relay the converters' tensor-memory stores to the MMA warp
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -358,10 +354,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int st = it % T_STAGES, as = it % g.naslot;
+        const int st = it % T_STAGES, as = st;
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-        uint64_t* slot_free = g.naslot == T_STAGES ? &empty[st] : &aempty[as];   // same ring when 4 slots
-        if (!mbar_wait(slot_free, ((it / g.naslot) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        // the slot is free once the MMAs of the stage's previous k-block are done; the TMA
+        // refill of the stage waited for the same release, so this wait passes at once
+        if (!mbar_wait(&empty[st], ((it / T_STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint4* row = (const uint4*)(A_f(st) + r * 128);
         float hi[32], lo[32];
@@ -429,8 +426,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       const bool mrow = m < g.M;
       const int64_t mo = mrow ? (m / g.om.mdiv) * g.om.c0 + (m % g.om.mdiv) * g.om.c1 : 0;
       for (int ch = 0; ch < nch; ++ch, ++lc) {
-        const int buf = lc & 1;
-        if (!mbar_wait(&accf[buf], (lc >> 1) & 1, abort_flag)) { ok = false; break; }
+        const int buf = lc % g.nbuf;
+        if (!mbar_wait(&accf[buf], (lc / g.nbuf) & 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
         for (int cb = 0; cb < BN; cb += 32) {
@@ -621,7 +618,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   g.ks = (int)((nk + g.nsplit - 1) / g.nsplit);
   g.nsplit = (int)((nk + g.ks - 1) / g.ks);   // every slice non-empty
   g.kch = g.ks <= 2 * KCH_BLOCKS ? g.ks : KCH_BLOCKS;
-  g.naslot = (g.ks + g.kch - 1) / g.kch == 1 ? 4 : 2;
+  g.nbuf = (g.ks + g.kch - 1) / g.kch == 1 ? 2 : 1;
   g.part = nullptr;
   if (g.nsplit > 1) {
     FP_CHECK(scratch_bytes >= gemm_tc_scratch_bytes(mode, M, N, K), FPEPS_ERR_ARG, "tensor-core GEMM: scratch too small");
