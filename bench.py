@@ -350,7 +350,7 @@ def main():
     # the kernel, from one ncu capture of the probe case (bench.py --probe-theta 8:
     # both GEMM launches, one sandwich launch); traffic per launch = ratio x the
     # algorithmic bytes of an average launch here (traffic grows with the bytes moved)
-    dram_per_alg_byte = {"gemm_tc_tf32x3": (0.911 + 1.020) / (2 * 0.966), "sandwich": 1.843 / 1.493}
+    dram_per_alg_byte = {"gemm_tc_tf32x3": (0.911 + 1.020) / (2 * 0.966), "sandwich": 1.837 / 1.493}
     traffic = None
     if dom in dram_per_alg_byte and d["launches"]:
         traffic = dram_per_alg_byte[dom] * d["bytes"] / d["launches"]
