@@ -96,7 +96,8 @@ void gemm_simt(cudaStream_t s, int64_t M, int64_t N, int64_t K, T alpha, const T
 // supported by the tensor-core path (caller falls back to nothing: it is an error).
 bool gemm_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb);
 void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
-             const float* B, int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes);
+             const float* B, int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes,
+             bool hold_loads = false);   // hold_loads: self-test of the bounded waits (no loads issued)
 size_t gemm_tc_scratch_bytes(int mode, int64_t M, int64_t N, int64_t K);
 
 // ---------------------------------------------------------------- sandwich

@@ -147,6 +147,7 @@ struct TcArgs {
   int nsplit;
   int kch;      // k-blocks per TMEM accumulation chunk
   int nbuf;     // TMEM chunk accumulators: 2 when every tile is one chunk, else 1 (+ running sum)
+  int hold;     // self-test of the bounded waits: issue no loads, so every consumer times out
   float* part;  // nsplit > 1: partial results [nsplit][M][N] row-major
 };
 
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
       int it = 0;
-      bool ok = true;
+      bool ok = !g.hold;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         int64_t m0, n0;
         tile_mn(tile, m0, n0);
@@ -596,7 +597,7 @@ size_t gemm_tc_scratch_bytes(int, int64_t M, int64_t N, int64_t K) {
 }
 
 void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
-             int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes) {
+             int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes, bool hold_loads) {
   FP_CHECK(mode == FPEPS_TF32X3, FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: only 3xTF32 is built");
   FP_CHECK(scratch && scratch_bytes >= sizeof(int), FPEPS_ERR_ARG, "tensor-core GEMM: scratch");
   FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
@@ -619,6 +620,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   g.nsplit = (int)((nk + g.ks - 1) / g.ks);   // every slice non-empty
   g.kch = g.ks <= 2 * KCH_BLOCKS ? g.ks : KCH_BLOCKS;
   g.nbuf = (g.ks + g.kch - 1) / g.kch == 1 ? 2 : 1;
+  g.hold = hold_loads ? 1 : 0;
   g.part = nullptr;
   if (g.nsplit > 1) {
     FP_CHECK(scratch_bytes >= gemm_tc_scratch_bytes(mode, M, N, K), FPEPS_ERR_ARG, "tensor-core GEMM: scratch too small");

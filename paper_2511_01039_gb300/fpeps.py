@@ -79,6 +79,7 @@ SIGNATURES = {
     "fpeps_svd_f64": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fpeps_svd_f64_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fpeps_launch_count": (C.c_int64, []),
+    "fpeps_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
     "fpeps_profile": (C.c_int, [C.c_int32]),
     "fpeps_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]),
@@ -257,6 +258,11 @@ PROF_KINDS = {0: "gemm_tc_tf32x3", 1: "gemm_simt", 2: "sandwich", 3: "gram", 4: 
 
 def fpeps_launch_count() -> int:
     return lib().fpeps_launch_count()
+
+
+def fpeps_selftest_wait_timeout(stream_handle: int = 0) -> int:
+    """Run the GEMM with its loads withheld; returns the status (ERR_TIMEOUT = the bounded waits worked)."""
+    return lib().fpeps_selftest_wait_timeout(stream_handle)
 
 
 def fpeps_profile(enable: bool):

@@ -1,4 +1,5 @@
-"""Full-size parity on sampled outputs (8x8, D=6, w=6 Hubbard FSM PEPO, chi=500).
+"""Full-size parity on sampled outputs (8x8, D=6, w=6 Hubbard FSM PEPO, chi=500,
+and the 6x6, D=6, w=4, chi=256 configuration).
 
 The oracle cannot run a whole chi=500 row in a test, but it can apply
 Theta_c of the central site to a few vectors: the GPU path (tensor-core GEMMs
@@ -14,16 +15,18 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("f32", 5e-5)])
-def test_central_site_theta_at_chi_500(prec, tol):
+@pytest.mark.parametrize("workload", ["C4", "C3"])
+def test_central_site_theta_full_size(prec, tol, workload):
+    """C4: 8x8, D=6, w=6, chi=500 (row 4); C3: 6x6, D=6, w=4, chi=256 (row 2)."""
     import torch
     from paper_2511_01039_gb300 import fpeps as fp
     from paper_2511_01039_gb300 import workloads as WL
     torch.cuda.set_device(0)
-    w = WL.hubbard_row(**WL.C4)
+    w = WL.hubbard_row(**getattr(WL, workload))
     env = fp.Env(w.peps, w.pepo, D=w.D, p=w.p, w=w.w, chi=w.chi, prec=prec, seed=1)
     fp.fpeps_import_boundary(env.h, WL.boundary_blob(w.boundary, w.row, 1, 4), w.row, 1)
     fp.fpeps_absorb_row(env.h, w.row, 1)
-    c = 3
+    c = w.Ly // 2 - 1
     A, W, T = w.peps[w.row][c], w.pepo[w.row][c], w.boundary[c]
     t, tp = T.shape[0], T.shape[2]
     dL, dR, dD = B.bdim(A, W, 0), B.bdim(A, W, 2), B.bdim(A, W, 3)
