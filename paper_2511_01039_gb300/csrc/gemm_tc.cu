@@ -15,6 +15,16 @@
 // thread and store hi and lo with tcgen05.st, so the MMAs take A from TMEM and
 // only B's hi/lo tiles from shared memory.
 //
+// Shared memory bandwidth bounds the single-CTA form: per 32-term k-block an SM
+// moves ~144 KB through it (TMA fills, the B split, the A rows, and 3 x 16 KB of B
+// read by the MMAs), ~1150 cycles at 128 B/clock against 768 cycles of MMAs. When
+// M spans more than one tile, CTA pairs (clusters of two, tcgen05 cta_group::2)
+// compute 256x128 tiles instead: each CTA holds 128 rows of A in its TMEM and 64
+// of the tile's 128 B rows in its shared memory, and rank 0 issues M=256 MMAs that
+// read B from both. B's loads, split and MMA reads per SM halve (~88 KB per
+// k-block). Converters and epilogue warps of both CTAs arrive on rank 0's
+// barriers; MMA completion is signalled to both CTAs by a multicast commit.
+//
 // Accumulation: the tensor cores' FP32 accumulation over long K loses far more
 // than round-to-nearest FP32 (measured ~1e-5 relative at K = 2048, ~1e-3 at
 // K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 256 terms; each
@@ -92,9 +102,49 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
   return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
+// Arrives on `bar` once the tcgen05 operations issued so far have completed. In the
+// CTA-pair form the arrival goes to the barrier at the same offset in every CTA
+// of `mask` (bit r = cluster rank r).
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit(uint64_t* bar, uint16_t mask = 1) {
+  if constexpr (PAIR) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+  } else {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of both CTAs of the pair
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// arrival on the barrier at the same shared-memory offset in the CTA of cluster
+// rank 0 (the CTA that issues the pair's MMAs). Default semantics (release at
+// CTA scope): a cluster-scope release is a memory barrier for the arriving warp
+// (the top stall of the converter warps when they used it). The data it
+// publishes is already complete when it arrives: TMEM stores are waited for
+// (tcgen05.wait::st) and shared-memory stores are fenced to the async proxy.
+__device__ __forceinline__ void mbar_arrive_rank0(uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .b32 ra;\n mapa.shared::cluster.u32 ra, %0, 0;\n"
+      " mbarrier.arrive.shared::cluster.b64 _, [ra];\n}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+// the converters and epilogue warps of both CTAs report to rank 0's barriers
+template <bool PAIR>
+__device__ __forceinline__ void mbar_arrive_issuer(uint64_t* bar, uint32_t rank) {
+  if (PAIR && rank != 0) mbar_arrive_rank0(bar);
+  else mbar_arrive(bar);
 }
 
 __device__ __forceinline__ uint32_t tf32_round(uint32_t bits) { return (bits + 0x1000u) & 0xFFFFE000u; }
@@ -167,7 +217,7 @@ constexpr int T_STAGE_BYTES = TILE_A + 2 * TILE_B;   // A fp32 | B hi (in place)
 constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024 + 256 + 4 * EPI_TILE * 4;
 constexpr uint32_t T_RUN = BN, T_ASLOT = 2 * BN;   // TMEM column bases (see the layout above)
 // warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue,
-// 16 waiter
+// 16 waiter; in a pair CTA 12..15 are a second set of A converters
 constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12, T_WAITER = 16;
 
 // named barrier 1 between the MMA warp and the waiter warp (64 threads); returns
@@ -182,18 +232,42 @@ __device__ __forceinline__ bool handoff_abort(bool mine) {
   return r != 0;
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
                                             uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc)
-      : "memory");
+  if constexpr (PAIR) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  }
 }
 
+template <bool PAIR>
 __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_constant__ CUtensorMap mapA,
                                                                 const __grid_constant__ CUtensorMap mapB, TcArgs g) {
-  if (*(volatile int*)g.err) return;
+  // CTA pair (cluster of two): each CTA holds 128 rows of a 256-row tile (A in its
+  // TMEM, accumulator in its TMEM) and half of the tile's B columns in its shared
+  // memory; rank 0 issues the M=256 MMAs for both.
+  constexpr int CS = PAIR ? 2 : 1;
+  constexpr int BNH = BN / CS;                 // B rows (output columns) held by this CTA
+  constexpr int TILE_BH = BNH * BK * 4;        // bytes
+  // A converter sets: each converts every NAS-th k-block, so a warp has NAS k-block
+  // periods for its load/split/TMEM-store chain. In a pair CTA warps 12..15 are the
+  // second set and B, halved per CTA, is converted by warps 6..7 alone.
+  constexpr int NAS = PAIR ? 2 : 1;
+  constexpr int NBW = PAIR ? 2 : T_NBCONV;
+  const uint32_t rank = PAIR ? cluster_rank() : 0;
+  const bool issuer = rank == 0;
+  // a CTA pair may not split up on a shared early exit, so only single CTAs return here
+  if (!PAIR && *(volatile int*)g.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + T_STAGES * T_STAGE_BYTES);
@@ -209,6 +283,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t ntiles = g.mt * g.nt * g.nsplit;
+  const int64_t tile0 = blockIdx.x / CS, tstep = gridDim.x / CS;
   const int nk_all = (int)((g.K + BK - 1) / BK);
   auto kslice = [&](int64_t tile, int& kb0, int& nk) {
     const int split = (int)(tile / (g.mt * g.nt));
@@ -222,32 +297,39 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     tile %= g.mt * g.nt;
     const int64_t mt = g.m_fast ? tile % g.mt : tile / g.nt;
     const int64_t nt = g.m_fast ? tile / g.mt : tile % g.nt;
-    m0 = mt * BM;
+    m0 = mt * (BM * CS) + rank * BM;
     n0 = nt * BN;
   };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < T_STAGES; ++st) {
       mbar_init(&full[st], 1);
-      mbar_init(&bconv[st], T_NBCONV);
+      mbar_init(&bconv[st], NBW * CS);
       mbar_init(&empty[st], 1);
     }
-    for (int b = 0; b < 4; ++b) mbar_init(&aconv[b], 4);
+    for (int b = 0; b < 4; ++b) mbar_init(&aconv[b], 4 * CS);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 4);
+      mbar_init(&acce[b], 4 * CS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(4 * BN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (PAIR) {   // one warp of each CTA of the pair, collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(4 * BN));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(4 * BN));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();   // the peer's barriers are initialised before any remote arrival
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   // A slots: columns [256, 512), one per stage
@@ -260,7 +342,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
       int it = 0;
       bool ok = !g.hold;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
         int64_t m0, n0;
         tile_mn(tile, m0, n0);
         int kb0, nk;
@@ -268,23 +350,24 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int st = it % T_STAGES;
           if (!mbar_wait(&empty[st], ((it / T_STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
-          mbar_arrive_expect_tx(&full[st], TILE_A + TILE_B);
+          mbar_arrive_expect_tx(&full[st], TILE_A + TILE_BH);
           tma_load_2d(A_f(st), &mapA, &full[st], (kb0 + kb) * BK, (int)m0);
-          tma_load_2d(B_hi(st), &mapB, &full[st], (kb0 + kb) * BK, (int)n0);
+          tma_load_2d(B_hi(st), &mapB, &full[st], (kb0 + kb) * BK, (int)(n0 + rank * BNH));
           ++issued;
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 && issuer) {
     // The MMA warp touches no shared memory while MMAs are in flight: an mbarrier
     // wait by the thread that issued tcgen05.mma stalls it until those MMAs have
     // drained (measured: one wait per 12 MMAs halves the tensor-pipe rate). The
     // waiter warp does the mbarrier waits and hands each ready k-block over on a
     // named barrier, whose OR-reduction also carries an abort.
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    const uint32_t idesc =
+        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((BM * CS) >> 4) << 24);
     int it = 0, lc = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
@@ -301,30 +384,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
               const uint64_t o = (uint64_t)(kk * 32) >> 4;
-              mma_tf32_ts(d, al + (uint32_t)(kk * 8), bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
-              mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
-              mma_tf32_ts(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
+              mma_tf32_ts<PAIR>(d, al + (uint32_t)(kk * 8), bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
+              mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
+              mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
             }
-            mma_commit(&empty[st]);   // frees the stage and its A slot
-            if (kb + 1 == c1) mma_commit(&accf[buf]);
+            mma_commit<PAIR>(&empty[st], (1u << CS) - 1);   // frees the stage and its A slot (both CTAs)
+            if (kb + 1 == c1) mma_commit<PAIR>(&accf[buf], (1u << CS) - 1);
           }
           __syncwarp();
         }
       }
     }
     if (lane == 0) {
-      mma_commit(drain);
+      mma_commit<PAIR>(drain, 1);
       const unsigned long long t0 = clock64();
       while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
       }
     }
     __syncwarp();
-  } else if (warp == T_WAITER) {
+  } else if (warp == T_WAITER && issuer) {
     // waits for the inputs of every k-block (and, at a chunk start, for the
     // accumulator buffer) in the MMA warp's order, then hands the k-block over
     int it = 0, lc = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
@@ -344,17 +427,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         }
       }
     }
-  } else if (warp < T_BCONV0) {
+  } else if ((warp >= 2 && warp < T_BCONV0) || (PAIR && warp >= T_BCONV1 && warp < T_WAITER)) {
     // A converters: thread = TMEM lane = tile row
     const int quarter = warp % 4;
+    const int set = warp >= T_BCONV1 ? 1 : 0;
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     int it = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int kb = 0; kb < nk; ++kb, ++it) {
+        if (NAS > 1 && it % NAS != set) continue;
         const int st = it % T_STAGES, as = st;
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
         // the slot is free once the MMAs of the stage's previous k-block are done; the TMA
@@ -380,15 +465,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&aconv[as]);
+        if (lane == 0) mbar_arrive_issuer<PAIR>(&aconv[as], rank);
       }
     }
-  } else if (warp < T_EPI0 || (warp >= T_BCONV1 && warp < T_WAITER)) {
+  } else if ((warp >= T_BCONV0 && warp < T_EPI0) || (!PAIR && warp >= T_BCONV1 && warp < T_WAITER)) {
     // B converters: hi in place, lo into the second B tile
     const int cw = warp < T_EPI0 ? warp - T_BCONV0 : warp - T_BCONV1 + (T_EPI0 - T_BCONV0);
     int it = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
       int kb0, nk;
       kslice(tile, kb0, nk);
       for (int kb = 0; kb < nk; ++kb, ++it) {
@@ -397,7 +482,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         uint4* bh = (uint4*)B_hi(st);
         uint4* blo = (uint4*)B_lo(st);
 #pragma unroll 3
-        for (int e = cw * 32 + lane; e < TILE_B / 16; e += T_NBCONV * 32) {
+        for (int e = cw * 32 + lane; e < TILE_BH / 16; e += NBW * 32) {
           const uint4 v = bh[e];
           const uint4 h = make_uint4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
           const uint4 l = make_uint4(tf32_round(__float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x))),
@@ -409,15 +494,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bconv[st]);
+        if (lane == 0) mbar_arrive_issuer<PAIR>(&bconv[st], rank);
       }
     }
-  } else {
+  } else if (warp >= T_EPI0 && warp < T_BCONV1) {
     const int q = warp - T_EPI0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     int lc = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
       int64_t m0, n0;
       tile_mn(tile, m0, n0);
       int kb0, nk;
@@ -483,7 +568,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acce[buf]);
+        if (lane == 0) mbar_arrive_issuer<PAIR>(&acce[buf], rank);
       }
     }
   }
@@ -504,9 +589,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     if (threadIdx.x == 0) atomicExch(g.err, 1);
   }
   __syncthreads();
+  // the pair's MMAs read this CTA's shared memory and write its TMEM, and the peer
+  // arrives on this CTA's barriers: neither CTA frees or exits before both are here
+  if constexpr (PAIR) cluster_sync_all();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * BN));
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * BN));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * BN));
   }
 }
 
@@ -590,10 +681,57 @@ static int sm_count() {
   return sms;
 }
 
+// CTA pairs the GPU holds at once (clusters of two CTAs, one CTA per SM); 0 if
+// the pair kernel cannot be launched
+static int pair_slots() {
+  static int n = -1;
+  if (n < 0) {
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_BYTES));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(sm_count() & ~1));
+    cfg.blockDim = dim3(P_THREADS);
+    cfg.dynamicSmemBytes = T_SMEM_BYTES;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, k_gemm_tf32x3_t<true>, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();
+      c = 0;
+    }
+    n = c;
+  }
+  return n;
+}
+
+// Tile schedule of one product: CTA pairs (256-row tiles) whenever M spans more
+// than one 128-row tile, single CTAs otherwise; K split only to fill the GPU.
+struct Plan {
+  bool pair;
+  int64_t mt, nt, slots;
+  int ks, nsplit;
+};
+static Plan plan_of(int64_t M, int64_t N, int64_t K) {
+  Plan p;
+  p.pair = M > BM && pair_slots() > 0;
+  const int cs = p.pair ? 2 : 1;
+  p.slots = p.pair ? pair_slots() : sm_count();
+  p.mt = (M + BM * cs - 1) / (BM * cs);
+  p.nt = (N + BN - 1) / BN;
+  const int64_t nk = (K + BK - 1) / BK;
+  const int ns = nsplit_of(p.mt * p.nt, K, (int)p.slots);
+  p.ks = (int)((nk + ns - 1) / ns);
+  p.nsplit = (int)((nk + p.ks - 1) / p.ks);   // every slice non-empty
+  return p;
+}
+
 size_t gemm_tc_scratch_bytes(int, int64_t M, int64_t N, int64_t K) {
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  const int ns = nsplit_of(tiles, K, sm_count());
-  return 256 + (ns > 1 ? (size_t)ns * M * N * sizeof(float) : 0);
+  const Plan p = plan_of(M, N, K);
+  return 256 + (p.nsplit > 1 ? (size_t)p.nsplit * M * N * sizeof(float) : 0);
 }
 
 void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
@@ -603,21 +741,19 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
   static bool attr = false;
   if (!attr) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_BYTES));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_BYTES));
     attr = true;
   }
-  const int sms = sm_count();
+  const Plan p = plan_of(M, N, K);
   CUtensorMap ma = make_map(A, M, K, lda, BM);
-  CUtensorMap mb = make_map(B, N, K, ldb, BN);
+  CUtensorMap mb = make_map(B, N, K, ldb, p.pair ? BN / 2 : BN);
   TcArgs g;
   g.M = M; g.N = N; g.K = K; g.om = om; g.C = C; g.err = (int*)scratch;
-  g.mt = (M + BM - 1) / BM;
-  g.nt = (N + BN - 1) / BN;
+  g.mt = p.mt;
+  g.nt = p.nt;
   g.m_fast = g.mt <= g.nt ? 1 : 0;
-  const int64_t nk = (K + BK - 1) / BK;
-  g.nsplit = nsplit_of(g.mt * g.nt, K, sms);
-  g.ks = (int)((nk + g.nsplit - 1) / g.nsplit);
-  g.nsplit = (int)((nk + g.ks - 1) / g.ks);   // every slice non-empty
+  g.ks = p.ks;
+  g.nsplit = p.nsplit;
   g.kch = g.ks <= 2 * KCH_BLOCKS ? g.ks : KCH_BLOCKS;
   g.nbuf = (g.ks + g.kch - 1) / g.kch == 1 ? 2 : 1;
   g.hold = hold_loads ? 1 : 0;
@@ -626,10 +762,26 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
     FP_CHECK(scratch_bytes >= gemm_tc_scratch_bytes(mode, M, N, K), FPEPS_ERR_ARG, "tensor-core GEMM: scratch too small");
     g.part = (float*)((char*)scratch + 256);
   }
-  const int64_t blocks = g.mt * g.nt * g.nsplit;
-  FP_CHECK(blocks < (1LL << 31), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: grid too large");
+  const int64_t tiles = g.mt * g.nt * g.nsplit;
+  FP_CHECK(tiles < (1LL << 30), FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: grid too large");
   ProfToken pt = prof_begin(PROF_GEMM_TC, s, 2.0 * M * N * K, 4.0 * ((double)M * K + (double)N * K + (double)M * N));
-  k_gemm_tf32x3_t<<<(unsigned)std::min<int64_t>(blocks, sms), P_THREADS, T_SMEM_BYTES, s>>>(ma, mb, g);
+  if (p.pair) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(tiles, p.slots)));
+    cfg.blockDim = dim3(P_THREADS);
+    cfg.dynamicSmemBytes = T_SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FP_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_tf32x3_t<true>, ma, mb, g));
+  } else {
+    k_gemm_tf32x3_t<false><<<(unsigned)std::min<int64_t>(tiles, p.slots), P_THREADS, T_SMEM_BYTES, s>>>(ma, mb, g);
+  }
   FP_LAUNCH();
   if (g.nsplit > 1) {
     const int64_t tot = M * N;
