@@ -196,7 +196,8 @@ struct TcArgs {
   int ks;       // k-blocks per K slice (split-K); nsplit = ceil(nk / ks)
   int nsplit;
   int kch;      // k-blocks per TMEM accumulation chunk
-  int nbuf;     // TMEM chunk accumulators: 2 when every tile is one chunk, else 1 (+ running sum)
+  int nbuf;     // TMEM chunk accumulators: 2 (alternating) when every tile is one chunk or the
+                // running sum is in shared memory (CTA pairs), else 1 (+ running sum in TMEM)
   int hold;     // self-test of the bounded waits: issue no loads, so every consumer times out
   float* part;  // nsplit > 1: partial results [nsplit][M][N] row-major
 };
@@ -213,8 +214,15 @@ struct TcArgs {
 // for the MMA warp.
 constexpr int P_THREADS = 544;
 constexpr int T_STAGES = 4;
-constexpr int T_STAGE_BYTES = TILE_A + 2 * TILE_B;   // A fp32 | B hi (in place) | B lo
-constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024 + 256 + 4 * EPI_TILE * 4;
+// Shared memory: the stage ring (A fp32 | B hi (in place) | B lo; a pair CTA holds
+// half of B, so its stages are 32 KB instead of 48), then in a pair CTA the
+// running FP32 sum of multi-chunk tiles (128 rows x 129 floats, padded so that a
+// row per lane is conflict-free), the barriers, and the epilogue's 32x33 tiles.
+template <bool PAIR> __host__ __device__ constexpr int t_stage_bytes() { return TILE_A + 2 * (PAIR ? TILE_B / 2 : TILE_B); }
+template <bool PAIR> __host__ __device__ constexpr int t_run_bytes() { return PAIR ? BM * (BN + 1) * 4 : 0; }
+template <bool PAIR> __host__ __device__ constexpr int t_bar_off() { return T_STAGES * t_stage_bytes<PAIR>() + t_run_bytes<PAIR>(); }
+template <bool PAIR> __host__ __device__ constexpr int t_smem_bytes() { return t_bar_off<PAIR>() + 256 + 4 * EPI_TILE * 4 + 1024; }
+static_assert(t_smem_bytes<false>() <= 227 * 1024 && t_smem_bytes<true>() <= 227 * 1024, "shared memory");
 constexpr uint32_t T_RUN = BN, T_ASLOT = 2 * BN;   // TMEM column bases (see the layout above)
 // warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue,
 // 16 waiter; in a pair CTA 12..15 are a second set of A converters
@@ -259,6 +267,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   constexpr int CS = PAIR ? 2 : 1;
   constexpr int BNH = BN / CS;                 // B rows (output columns) held by this CTA
   constexpr int TILE_BH = BNH * BK * 4;        // bytes
+  constexpr int T_STAGE_BYTES = t_stage_bytes<PAIR>();
   // A converter sets: each converts every NAS-th k-block, so a warp has NAS k-block
   // periods for its load/split/TMEM-store chain. In a pair CTA warps 12..15 are the
   // second set and B, halved per CTA, is converted by warps 6..7 alone.
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   if (!PAIR && *(volatile int*)g.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + T_STAGES * T_STAGE_BYTES);
+  uint64_t* full = (uint64_t*)(smem + t_bar_off<PAIR>());
   uint64_t* bconv = full + T_STAGES;
   uint64_t* empty = bconv + T_STAGES;
   uint64_t* aconv = empty + T_STAGES;   // [4] A slot filled (A slot = stage index; freed with the stage)
@@ -279,7 +288,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   uint64_t* drain = acce + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  float* epi_tiles = (float*)(smem + T_STAGES * T_STAGE_BYTES + 256);
+  float* epi_tiles = (float*)(smem + t_bar_off<PAIR>() + 256);
+  float* run_sum = (float*)(smem + T_STAGES * T_STAGE_BYTES);   // pair CTA: [BM][BN + 1]
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t ntiles = g.mt * g.nt * g.nsplit;
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   };
   auto A_f = [&](int st) { return smem + st * T_STAGE_BYTES; };
   auto B_hi = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A; };
-  auto B_lo = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A + TILE_B; };
+  auto B_lo = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A + TILE_BH; };
   auto tile_mn = [&](int64_t tile, int64_t& m0, int64_t& n0) {
     tile %= g.mt * g.nt;
     const int64_t mt = g.m_fast ? tile % g.mt : tile / g.nt;
@@ -524,6 +534,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             tmem_wait32(rc);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rc[j]);
+          } else if constexpr (PAIR) {
+            const float* rs = run_sum + (q * 32 + lane) * (BN + 1) + cb;
+            tmem_wait32(rc);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = rs[j] + __uint_as_float(rc[j]);
           } else {
             tmem_ld32_async(tmem + lane_base + T_RUN + (uint32_t)cb, rr);
             tmem_wait32(rc);
@@ -532,7 +547,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]) + __uint_as_float(rc[j]);
           }
           if (ch + 1 < nch) {
-            tmem_st32(tmem + lane_base + T_RUN + (uint32_t)cb, v);
+            if constexpr (PAIR) {
+              float* rs = run_sum + (q * 32 + lane) * (BN + 1) + cb;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) rs[j] = v[j];
+            } else {
+              tmem_st32(tmem + lane_base + T_RUN + (uint32_t)cb, v);
+            }
           } else if (!__shfl_sync(0xffffffffu, *abort_flag, 0)) {   // warp-uniform decision
             if (g.nsplit > 1 || g.om.c3 == 1) {
               float* tw = epi_tiles + q * EPI_TILE;
@@ -686,11 +707,12 @@ static int sm_count() {
 static int pair_slots() {
   static int n = -1;
   if (n < 0) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_BYTES));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 t_smem_bytes<true>()));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(sm_count() & ~1));
     cfg.blockDim = dim3(P_THREADS);
-    cfg.dynamicSmemBytes = T_SMEM_BYTES;
+    cfg.dynamicSmemBytes = t_smem_bytes<true>();
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2;
@@ -741,7 +763,8 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
   static bool attr = false;
   if (!attr) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_BYTES));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 t_smem_bytes<false>()));
     attr = true;
   }
   const Plan p = plan_of(M, N, K);
@@ -755,7 +778,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   g.ks = p.ks;
   g.nsplit = p.nsplit;
   g.kch = g.ks <= 2 * KCH_BLOCKS ? g.ks : KCH_BLOCKS;
-  g.nbuf = (g.ks + g.kch - 1) / g.kch == 1 ? 2 : 1;
+  g.nbuf = (p.pair || (g.ks + g.kch - 1) / g.kch == 1) ? 2 : 1;
   g.hold = hold_loads ? 1 : 0;
   g.part = nullptr;
   if (g.nsplit > 1) {
@@ -769,7 +792,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(tiles, p.slots)));
     cfg.blockDim = dim3(P_THREADS);
-    cfg.dynamicSmemBytes = T_SMEM_BYTES;
+    cfg.dynamicSmemBytes = t_smem_bytes<true>();
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -780,7 +803,8 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
     cfg.numAttrs = 1;
     FP_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_tf32x3_t<true>, ma, mb, g));
   } else {
-    k_gemm_tf32x3_t<false><<<(unsigned)std::min<int64_t>(tiles, p.slots), P_THREADS, T_SMEM_BYTES, s>>>(ma, mb, g);
+    k_gemm_tf32x3_t<false><<<(unsigned)std::min<int64_t>(tiles, p.slots), P_THREADS, t_smem_bytes<false>(), s>>>(ma, mb,
+                                                                                                             g);
   }
   FP_LAUNCH();
   if (g.nsplit > 1) {
