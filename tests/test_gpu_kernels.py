@@ -1,6 +1,8 @@
 """Kernel-level parity through the C ABI (fpeps_gemm_f32): the tensor-core
 3xTF32 GEMM and the CUDA-core FP32 GEMM against an FP64 evaluation of the same
-product, on ragged shapes that span several 128x128x32 tiles."""
+product, on ragged shapes that span several 128x128x32 tiles. Products with
+M <= 128 run on single CTAs, larger ones on CTA pairs (256-row tiles); M = 129
+and 257 leave most rows of a pair's second CTA outside the matrix."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +20,8 @@ def fp():
 @pytest.mark.parametrize("M,N,K,pad", [(300, 260, 100, 0), (128, 128, 32, 0), (1000, 2000, 512, 4),
                                        (4100, 700, 1000, 12), (130, 4097, 36, 0), (500, 432, 108000, 0),
                                        (260, 300, 4100, 8), (500, 60, 108000, 0), (64, 256, 1000, 0),
-                                       (1, 9, 40, 0), (3000, 7, 500, 4)])
+                                       (1, 9, 40, 0), (3000, 7, 500, 4), (129, 300, 2000, 0),
+                                       (257, 64, 33, 4)])
 @pytest.mark.parametrize("mode", ["tf32x3", "f32"])
 def test_gemm_against_fp64(fp, M, N, K, pad, mode):
     import torch
