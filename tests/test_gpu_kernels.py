@@ -21,7 +21,7 @@ def fp():
                                        (4100, 700, 1000, 12), (130, 4097, 36, 0), (500, 432, 108000, 0),
                                        (260, 300, 4100, 8), (500, 60, 108000, 0), (64, 256, 1000, 0),
                                        (1, 9, 40, 0), (3000, 7, 500, 4), (129, 300, 2000, 0),
-                                       (257, 64, 33, 4)])
+                                       (257, 64, 33, 3)])
 @pytest.mark.parametrize("mode", ["tf32x3", "f32"])
 def test_gemm_against_fp64(fp, M, N, K, pad, mode):
     import torch
