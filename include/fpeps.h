@@ -224,13 +224,15 @@ fpeps_status fpeps_svd_f64(const double* M, int32_t k, double* U, double* sigma,
 fpeps_status fpeps_svd_f64_noalloc(const double* M, int32_t k, double* U, double* sigma, double* V,
                                    void* cuda_stream);
 
-/* Self-test of the failure path (diagnostic): launches the tensor-core GEMM on a
- * 128 x 128 x 32 product with its loads withheld, so that every bounded wait in
- * the kernel (about one second each) runs out; the kernel sets its error word,
- * frees its tensor memory and exits, and the context stays usable. Returns
- * FPEPS_ERR_TIMEOUT when that path worked as designed (FPEPS_OK would mean a wait
- * did not notice the missing data). Allocates its buffers with cudaMallocAsync
- * on `cuda_stream` and synchronises it. The paper has no counterpart. */
+/* Self-test of the failure path (diagnostic): launches the tensor-core GEMM with
+ * its loads withheld, on a 128 x 128 x 32 product (single CTA) and on a
+ * 256 x 128 x 32 product (CTA pair), so that every bounded wait in the kernel
+ * (about one second each) runs out; the kernel sets its error word, frees its
+ * tensor memory and exits, and the context stays usable. Returns
+ * FPEPS_ERR_TIMEOUT when both launches took that path as designed (FPEPS_OK
+ * means a wait did not notice the missing data). Allocates its buffers with
+ * cudaMallocAsync on `cuda_stream` and synchronises it. The paper has no
+ * counterpart. */
 fpeps_status fpeps_selftest_wait_timeout(void* cuda_stream);
 
 /* Number of kernels this library has launched in the process so far. */

@@ -506,27 +506,32 @@ fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void*
 fpeps_status fpeps_selftest_wait_timeout(void* cuda_stream) {
   return fpeps::guard(nullptr, [&] {
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int64_t M = 128, N = 128, K = 32;
-    float *A = nullptr, *B = nullptr, *C = nullptr;
-    const size_t sb = fpeps::gemm_tc_scratch_bytes(FPEPS_TF32X3, M, N, K);
-    int* err = nullptr;
-    FP_CUDA(cudaMallocAsync((void**)&A, sizeof(float) * M * K, s));
-    FP_CUDA(cudaMallocAsync((void**)&B, sizeof(float) * N * K, s));
-    FP_CUDA(cudaMallocAsync((void**)&C, sizeof(float) * M * N, s));
-    FP_CUDA(cudaMallocAsync((void**)&err, sb, s));
-    FP_CUDA(cudaMemsetAsync(A, 0, sizeof(float) * M * K, s));
-    FP_CUDA(cudaMemsetAsync(B, 0, sizeof(float) * N * K, s));
-    FP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    fpeps::gemm_tc(s, FPEPS_TF32X3, M, N, K, A, K, B, K, C, fpeps::out_rowmajor(M, N, N), err, sb, true);
-    int h = 0;
-    FP_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FP_CUDA(cudaStreamSynchronize(s));
-    cudaFreeAsync(A, s);
-    cudaFreeAsync(B, s);
-    cudaFreeAsync(C, s);
-    cudaFreeAsync(err, s);
-    FP_CUDA(cudaStreamSynchronize(s));
-    if (h) throw Error{FPEPS_ERR_TIMEOUT, "tensor-core GEMM: bounded waits ran out as designed"};
+    // a 128-row product runs on a single CTA, a 256-row one on a CTA pair
+    int timed_out = 0;
+    for (const int64_t M : {128, 256}) {
+      const int64_t N = 128, K = 32;
+      float *A = nullptr, *B = nullptr, *C = nullptr;
+      const size_t sb = fpeps::gemm_tc_scratch_bytes(FPEPS_TF32X3, M, N, K);
+      int* err = nullptr;
+      FP_CUDA(cudaMallocAsync((void**)&A, sizeof(float) * M * K, s));
+      FP_CUDA(cudaMallocAsync((void**)&B, sizeof(float) * N * K, s));
+      FP_CUDA(cudaMallocAsync((void**)&C, sizeof(float) * M * N, s));
+      FP_CUDA(cudaMallocAsync((void**)&err, sb, s));
+      FP_CUDA(cudaMemsetAsync(A, 0, sizeof(float) * M * K, s));
+      FP_CUDA(cudaMemsetAsync(B, 0, sizeof(float) * N * K, s));
+      FP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+      fpeps::gemm_tc(s, FPEPS_TF32X3, M, N, K, A, K, B, K, C, fpeps::out_rowmajor(M, N, N), err, sb, true);
+      int h = 0;
+      FP_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FP_CUDA(cudaStreamSynchronize(s));
+      cudaFreeAsync(A, s);
+      cudaFreeAsync(B, s);
+      cudaFreeAsync(C, s);
+      cudaFreeAsync(err, s);
+      FP_CUDA(cudaStreamSynchronize(s));
+      timed_out += h != 0;
+    }
+    if (timed_out == 2) throw Error{FPEPS_ERR_TIMEOUT, "tensor-core GEMM: bounded waits ran out as designed"};
   });
 }
 

@@ -76,15 +76,16 @@ def test_svd_f64_against_lapack(fp, k):
 
 def test_bounded_waits_time_out_and_context_survives(fp):
     """Failure detection without a GPU fault: the GEMM runs with its TMA loads
-    withheld, every mbarrier wait runs out after its bound (~1 s), the kernel
-    reports ERR_TIMEOUT through its error word, and the next product on the same
-    context is correct."""
+    withheld (on a single CTA and on a CTA pair), every mbarrier wait runs out
+    after its bound (~1 s), the kernel reports ERR_TIMEOUT through its error word,
+    and the next products on the same context are correct."""
     import torch
     assert fp.fpeps_selftest_wait_timeout() == 6      # FPEPS_ERR_TIMEOUT
     g = torch.Generator(device="cuda").manual_seed(3)
-    A = torch.randn(256, 64, device="cuda", generator=g)
-    B = torch.randn(200, 64, device="cuda", generator=g)
-    C = torch.empty(256, 200, device="cuda")
-    fp.fpeps_gemm_f32(fp.TF32X3, A, B, C)
-    ref = A.double() @ B.double().T
-    assert ((C.double() - ref).abs().max() / ref.abs().max()).item() < 1e-5
+    for M in (100, 300):
+        A = torch.randn(M, 64, device="cuda", generator=g)
+        B = torch.randn(200, 64, device="cuda", generator=g)
+        C = torch.empty(M, 200, device="cuda")
+        fp.fpeps_gemm_f32(fp.TF32X3, A, B, C)
+        ref = A.double() @ B.double().T
+        assert ((C.double() - ref).abs().max() / ref.abs().max()).item() < 1e-5
