@@ -373,8 +373,11 @@ def main():
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom}
+    # achieved TFLOP/s and GB/s (algorithmic flops and bytes / device time) per kernel class;
+    # the sketch and the Gram pass of the QR stream their operand through HBM once
     per_kind = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                    "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None} for k, v in prof.items()}
+                    "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
+                    "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None} for k, v in prof.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world if dist else args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -244,7 +244,8 @@ int64_t fpeps_launch_count(void);
  * launches of one class, their count, summed device time (ms), summed
  * algorithmic flops and summed algorithmic bytes; it synchronises on the
  * recorded events. kind: 0 tensor-core GEMM, 1 CUDA-core GEMM, 2 sandwich,
- * 3 Gram, 4 small factorisations (Cholesky, inverse, Jacobi). */
+ * 3 Gram, 4 small factorisations (Cholesky, inverse, Jacobi), 5 Gaussian
+ * sketch (flops 0, bytes = the sketch matrix written). */
 fpeps_status fpeps_profile(int32_t enable);
 fpeps_status fpeps_profile_read(int32_t kind, int64_t* launches, double* ms, double* flops, double* bytes);
 

@@ -33,7 +33,9 @@ struct Error {
 // Every kernel launch of the library goes through FP_LAUNCH (count), and the
 // hot kernel classes can be bracketed with CUDA events (prof_begin/prof_end)
 // when profiling is enabled, so callers can time them on their own stream.
-enum ProfKind { PROF_GEMM_TC = 0, PROF_GEMM_SIMT = 1, PROF_SANDWICH = 2, PROF_GRAM = 3, PROF_FACTOR = 4, PROF_KINDS = 5 };
+enum ProfKind {
+  PROF_GEMM_TC = 0, PROF_GEMM_SIMT = 1, PROF_SANDWICH = 2, PROF_GRAM = 3, PROF_FACTOR = 4, PROF_SKETCH = 5, PROF_KINDS = 6
+};
 void count_launch();
 struct ProfToken {
   int kind = -1;

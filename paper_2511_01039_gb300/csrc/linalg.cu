@@ -682,8 +682,11 @@ template <class T>
 void gaussian_sketch(cudaStream_t s, T* out, int64_t n_rows, int64_t k, int64_t ld, const int64_t* perm_div,
                      uint64_t seed, uint64_t layer, uint64_t w2, uint64_t w3) {
   int64_t hi = perm_div ? perm_div[0] : 1, lo = perm_div ? perm_div[1] : n_rows;
+  // algorithmic bytes: the n x k matrix written once (the draws are FP64 arithmetic)
+  ProfToken pt = prof_begin(PROF_SKETCH, s, 0.0, (double)sizeof(T) * n_rows * k);
   k_sketch<T><<<grid_for(n_rows * k), 256, 0, s>>>(out, n_rows, k, ld, hi, lo, perm_div ? 1 : 0, seed, layer, w2, w3);
   FP_LAUNCH();
+  prof_end(pt, s);
 }
 
 template <class T>

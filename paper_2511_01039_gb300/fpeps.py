@@ -253,7 +253,7 @@ def fpeps_svd_f64_noalloc(M, stream_handle: int = 0):
     return U.t(), s, V.t()
 
 
-PROF_KINDS = {0: "gemm_tc_tf32x3", 1: "gemm_simt", 2: "sandwich", 3: "gram", 4: "factor"}
+PROF_KINDS = {0: "gemm_tc_tf32x3", 1: "gemm_simt", 2: "sandwich", 3: "gram", 4: "factor", 5: "sketch"}
 
 
 def fpeps_launch_count() -> int:
