@@ -32,17 +32,18 @@ design notes):
     singular value, so the new bond is sector-contiguous;
   * the null test and the sign gauge are those of the dense zip-up, applied to
     the sector vectors embedded in the full row / column space;
-  * the CBE fit (Fig. 3-5) is not part of this mode yet: rows are absorbed by
-    the zip-up alone (n_fit = 0).
+  * the CBE fit (Fig. 3-5) runs sector by sector in the same way (see
+    ``cbe_fit_u1``).
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 
 import numpy as np
 
 from .boundary import (NULL_TOL, RsvdParams, RowResult, bdim, close_last_row, first_row_boundary, gauge_signs,
-                       rsvd, theta, theta_t)
+                       orth, rsvd, theta, theta_r, theta_r_t, theta_t)
 from .philox import gaussian_sketch
 
 
@@ -61,11 +62,13 @@ def _sectors(rowq: np.ndarray, colq: np.ndarray):
     return sorted({tuple(x) for x in rowq.tolist()} & {tuple(x) for x in colq.tolist()})
 
 
-def sector_rsvd(ap, ap_t, rowq, colq, chi: int, prm: RsvdParams, omega_of):
+def sector_rsvd(ap, ap_t, rowq, colq, chi: int, prm: RsvdParams, omega_of, cap_of=None):
     """rSVD of a block-diagonal matrix, sector by sector, with one global truncation.
 
     ap / ap_t apply the dense matrix and its transpose to column blocks;
-    omega_of(k) returns the dense sketch (cols x k). Returns (U, s, Vt, q, alive): the
+    omega_of(k) returns the dense sketch (cols x k); cap_of(q, ri, ci) bounds the
+    triplets a sector may offer (default min(chi, rows_Q, cols_Q)); the total kept is
+    min(chi, sum of the caps). Returns (U, s, Vt, q, alive): the
     kept left vectors embedded in the row space (rows x chi_c), their singular
     values, the right vectors embedded in the column space (chi_c x cols), the
     sector charge of each kept triplet (chi_c x 2) and the null test of the dense
@@ -77,13 +80,16 @@ def sector_rsvd(ap, ap_t, rowq, colq, chi: int, prm: RsvdParams, omega_of):
         ri = np.flatnonzero(np.all(rowq == qc, axis=1))
         ci = np.flatnonzero(np.all(colq == qc, axis=1))
         rank = min(len(ri), len(ci))
-        k = rank if prm.exact_svd else min(chi + prm.oversample, rank)
-        sec.append((qc, ri, ci, rank, k))
+        cap = min(chi, rank) if cap_of is None else max(0, min(chi, rank, cap_of(qc, ri, ci)))
+        if cap == 0:
+            continue
+        k = rank if prm.exact_svd else min(cap + prm.oversample, rank)
+        sec.append((qc, ri, ci, cap, k))
     if not sec:
         raise ValueError("no charge sector is shared by the rows and columns")
     omega = omega_of(max(s[4] for s in sec))
     parts = []
-    for qc, ri, ci, rank, k in sec:
+    for qc, ri, ci, cap, k in sec:
         out_r = np.ones(rows, dtype=bool)
         out_r[ri] = False
         out_c = np.ones(cols, dtype=bool)
@@ -106,10 +112,9 @@ def sector_rsvd(ap, ap_t, rowq, colq, chi: int, prm: RsvdParams, omega_of):
             return Z[ci]
 
         Q, ub, s, vt = rsvd(ap_s, ap_t_s, omega[ci, :k], prm.power_iters)
-        parts.append((qc, ri, ci, min(chi, rank), Q @ ub, s, vt))
+        parts.append((qc, ri, ci, cap, Q @ ub, s, vt))
 
-    total_rank = sum(min(len(p[1]), len(p[2])) for p in parts)
-    chi_c = min(chi, total_rank)
+    chi_c = min(chi, sum(p[3] for p in parts))
     cand = [(-s[j], n, j) for n, (_, _, _, cap, _, s, _) in enumerate(parts) for j in range(cap)]
     kept = sorted(sorted(cand)[:chi_c], key=lambda x: (x[1], x[2]))
     U = np.zeros((rows, chi_c))
@@ -125,6 +130,39 @@ def sector_rsvd(ap, ap_t, rowq, colq, chi: int, prm: RsvdParams, omega_of):
     tot = float(sum((p[5] ** 2).sum() for p in parts))
     alive = ((sv * sv > NULL_TOL * tot) & (tot > 0)).astype(np.float64)
     return U, sv, Vt, qk, alive
+
+
+def sector_svd(M: np.ndarray, rowq, colq, keep_max: int):
+    """Exact SVD of a block-diagonal matrix sector by sector, the keep_max largest
+    triplets kept over all sectors (ordered by sector, then value). Returns
+    (U, s, Wt, q, alive) embedded in the full row / column spaces."""
+    rows, cols = M.shape
+    parts = []
+    allowed = np.zeros((rows, cols), dtype=bool)
+    for qc in _sectors(rowq, colq):
+        ri = np.flatnonzero(np.all(rowq == qc, axis=1))
+        ci = np.flatnonzero(np.all(colq == qc, axis=1))
+        allowed[np.ix_(ri, ci)] = True
+        u, sv, wt = np.linalg.svd(M[np.ix_(ri, ci)], full_matrices=False)
+        parts.append((qc, ri, ci, u, sv, wt))
+    if np.any(M[~allowed] != 0):
+        raise AssertionError("matrix is not block diagonal in the given charges")
+    keep = min(keep_max, sum(len(p[4]) for p in parts))
+    cand = [(-p[4][j], n, j) for n, p in enumerate(parts) for j in range(len(p[4]))]
+    kept = sorted(sorted(cand)[:keep], key=lambda x: (x[1], x[2]))
+    U = np.zeros((rows, keep))
+    Wt = np.zeros((keep, cols))
+    sv_k = np.zeros(keep)
+    qk = np.zeros((keep, 2), dtype=np.int64)
+    for m, (_, n, j) in enumerate(kept):
+        qc, ri, ci, u, sv, wt = parts[n]
+        U[ri, m] = u[:, j]
+        Wt[m, ci] = wt[j]
+        sv_k[m] = sv[j]
+        qk[m] = qc
+    tot = float(sum((p[4] ** 2).sum() for p in parts))
+    alive = ((sv_k * sv_k > NULL_TOL * tot) & (tot > 0)).astype(np.float64)
+    return U, sv_k, Wt, qk, alive
 
 
 def zipup_u1(T, qT, Arow, Wrow, qrow, chi: int, prm: RsvdParams, *, seed: int, layer: int, row: int,
@@ -182,6 +220,112 @@ def zipup_u1(T, qT, Arow, Wrow, qrow, chi: int, prm: RsvdParams, *, seed: int, l
     return N, ELs, log_s, spectra, qN
 
 
+def cbe_fit_u1(T, qT, Arow, Wrow, qrow, N, qN, ELs, chi: int, prm: RsvdParams, *, seed: int, layer: int,
+               row: int, env: int = 0):
+    """Right-to-left CBE fit in the block-sparse mode (the form of ``boundary.cbe_fit``).
+
+    Every matrix of the fit is block diagonal in the charge of the bond a_{c-1} it
+    straddles: the rows of the centre tensor (their ordered Gram-Schmidt keeps
+    sectors apart, the rows having disjoint supports), the CBE matrix
+    A = P_L^perp Theta2s P_R^perp (sector-wise rSVD; a sector offers at most
+    min(chi_tilde, rows_Q - n_Q(a_{c-1}), cols_Q - n_Q(V)) triplets and chi_tilde are
+    kept over all sectors) and the fitted tensor M' (sector-wise SVD, chi kept over
+    all sectors). Returns (new T, log_scale, spectra, bond charges).
+    """
+    Ly = len(T)
+    chi_t = prm.chi_tilde if prm.chi_tilde > 0 else -(-chi // 10)
+    M = N[Ly - 1]
+    qright = np.zeros((1, 2), dtype=np.int64)      # charges of bond a_c (right of the centre)
+    ER = np.ones((1, 1, 1))
+    rs = 0.0
+    rs_M = 0.0
+    out = [None] * Ly
+    qout = [None] * Ly
+    qout[Ly - 1] = qright
+    spectra = []
+    zero = np.zeros((1, 2), dtype=np.int64)
+    for c in range(Ly - 1, 0, -1):
+        A, W = Arow[c], Wrow[c]
+        Al, Wl = Arow[c - 1], Wrow[c - 1]
+        a_prev, dDn, a_c = M.shape
+        QD, QDl = qrow[c][3], qrow[c - 1][3]
+        qa_prev = qN[c - 1]
+        qa_left = qN[c - 2] if c >= 2 else zero
+        colq = (QD[:, None, :] + qright[None, :, :]).reshape(-1, 2)          # (Dn_c, a_c)
+        if a_prev >= dDn * a_c:
+            V = np.eye(dDn * a_c)
+            qV = colq
+        else:
+            V = orth(M.reshape(a_prev, dDn * a_c).T).T
+            qV = qa_prev
+        Nl = N[c - 1]
+        Nlm = Nl.reshape(-1, Nl.shape[2])
+        rows_a, cols_a = Nlm.shape[0], dDn * a_c
+        rowq = (qa_left[:, None, :] - QDl[None, :, :]).reshape(-1, 2)        # (a_{c-2}, Dn_{c-1})
+        ELl = ELs[c - 1]
+        a2, dDnl = ELl.shape[0], bdim(Al, Wl, 3)
+
+        def two_site(X, ER=ER):
+            z = theta_r(ER, T[c], A, W, X.reshape(dDn, a_c, -1))
+            return theta(ELl, T[c - 1], Al, Wl, z).reshape(rows_a, -1)
+
+        def two_site_t(Y, ER=ER):
+            z = theta_t(ELl, T[c - 1], Al, Wl, Y.reshape(a2, dDnl, -1))
+            return theta_r_t(ER, T[c], A, W, z).reshape(cols_a, -1)
+
+        def a_apply(X):
+            y = two_site(X) - two_site(V.T @ (V @ X))
+            return y - Nlm @ (Nlm.T @ y)
+
+        def a_apply_t(Y):
+            z = two_site_t(Y) - two_site_t(Nlm @ (Nlm.T @ Y))
+            return z - V.T @ (V @ z)
+
+        def cap_of(qc, ri, ci):
+            n_a = int(np.all(qa_prev == qc, axis=1).sum())
+            n_v = int(np.all(qV == qc, axis=1).sum())
+            return min(chi_t, len(ri) - n_a, len(ci) - n_v)
+
+        caps = [cap_of(qc, np.flatnonzero(np.all(rowq == qc, axis=1)), np.flatnonzero(np.all(colq == qc, axis=1)))
+                for qc in _sectors(rowq, colq)]
+        ct = min(chi_t, sum(max(0, x) for x in caps))
+        if ct > 0:
+            def omega_of(k, c=c):
+                return gaussian_sketch(cols_a, k, seed=seed, layer=layer, stage=1, site=c, row=row, env=env)
+
+            # as in the dense fit, the CBE sketch keeps its width chi_tilde + oversample
+            # whatever exact_svd says (that setting governs the zip-up)
+            cbe_prm = dataclasses.replace(prm, exact_svd=False)
+            _, sa, vt, qt, alive = sector_rsvd(a_apply, a_apply_t, rowq, colq, ct, cbe_prm, omega_of, cap_of)
+            vt = vt * alive[:, None]
+            Vp = orth(np.hstack([V.T, vt.T])).T
+            qVp = np.concatenate([qV, qt])
+        else:
+            Vp, qVp = V, qV
+        ERp = theta_r(ER, T[c], A, W, Vp.T.reshape(dDn, a_c, -1))
+        Mp = theta(ELl, T[c - 1], Al, Wl, ERp).reshape(a2 * dDnl, -1)
+        u, s, wt, qk, alive = sector_svd(Mp, rowq, qVp, chi)
+        wt = wt * alive[:, None]
+        keep = len(s)
+        nc = wt @ Vp
+        sg = gauge_signs(nc, 1, seed=seed, layer=layer, site=c, row=row, env=env)
+        nc = nc * sg[:, None]
+        out[c] = nc.reshape(keep, dDn, a_c)
+        M = ((u * s) * sg[None, :]).reshape(a2, dDnl, keep)
+        er = (sg[:, None] * wt) @ ERp.reshape(-1, ERp.shape[2]).T
+        nrm = np.linalg.norm(er)
+        rs_M = rs
+        rs += math.log(nrm)
+        ER = (er / nrm).reshape(keep, ERp.shape[0], ERp.shape[1])
+        spectra.append(s.copy())
+        qright = qk
+        qout[c - 1] = qk
+    nrm = np.linalg.norm(M)
+    out[0] = M / nrm
+    spectra.reverse()
+    return out, rs_M + math.log(nrm), spectra, qout
+
+
 def first_row_charges(qrow):
     """Bond charges of the exact row-0 boundary: q_{t_c} = Q_R of site c (right edge trivial)."""
     return [qr for (_, _, qr, _) in qrow[:-1]] + [np.zeros((1, 2), dtype=np.int64)]
@@ -193,8 +337,8 @@ def contract_u1(peps, qpeps, pepo, qpepo, chi: int, prm: RsvdParams, *, seed: in
 
     qpeps[r][c] / qpepo[r][c]: (q_l, q_u, q_r, q_d) leg charges of the PEPS / PEPO site.
     """
-    if prm.n_fit != 0:
-        raise ValueError("the symmetric mode absorbs rows by the zip-up alone (n_fit = 0)")
+    if prm.n_fit not in (0, 1):
+        raise ValueError("n_fit must be 0 or 1")
     Lx, Ly = len(peps), len(peps[0])
     bundles = [[site_bundles(qpeps[r][c], qpepo[r][c]) for c in range(Ly)] for r in range(Lx)]
     rows = []
@@ -205,11 +349,16 @@ def contract_u1(peps, qpeps, pepo, qpepo, chi: int, prm: RsvdParams, *, seed: in
     T, log_total = first_row_boundary(peps[0], pepo[0])
     qT = first_row_charges(bundles[0])
     for r in range(1, Lx - 1):
-        N, _, log_s, zsp, qT = zipup_u1(T, qT, peps[r], pepo[r], bundles[r], chi, prm, seed=seed, layer=layer,
-                                        row=r, env=env)
-        T = N
+        N, ELs, log_s, zsp, qN = zipup_u1(T, qT, peps[r], pepo[r], bundles[r], chi, prm, seed=seed, layer=layer,
+                                          row=r, env=env)
+        if prm.n_fit == 1 and Ly > 1:
+            N, log_s, fsp, qN = cbe_fit_u1(T, qT, peps[r], pepo[r], bundles[r], N, qN, ELs, chi, prm, seed=seed,
+                                           layer=layer, row=r, env=env)
+        else:
+            fsp = []
+        T, qT = N, qN
         log_total += log_s
-        rows.append(RowResult(N, log_s, zsp, []))
+        rows.append(RowResult(N, log_s, zsp, fsp))
     sign, lv = close_last_row(T, peps[Lx - 1], pepo[Lx - 1])
     log_total += lv
     return (sign, log_total, rows) if return_rows else (sign, log_total)
