@@ -14,7 +14,10 @@ What fixes it independently of its own code:
   * the new boundary tensors conserve charge with the bond charges returned,
     after the zip-up and after the fit;
   * a wrong sign in the bundle charge (a planted mistake) is caught by the
-    block-diagonality check.
+    block-diagonality check;
+  * in the approximate regime (a sector's rank above the sketch width) the kept
+    Ritz values never exceed the exact singular values (interlacing) and the
+    kept vectors are orthonormal and sector-pure.
 """
 import numpy as np
 import pytest
@@ -166,3 +169,36 @@ def test_fitted_boundary_conserves_charge():
         assert nz.any()
         assert np.all(np.all(bal == 0, axis=-1)[nz])
         qa = qF[c]
+
+
+def test_sector_rsvd_ritz_values_bounded_by_exact():
+    """Approximate regime (sectors wider than the sketch): every kept Ritz value is at most
+    the exact singular value of the same rank (interlacing within each sector, hence
+    for the sorted union), and the kept vectors are orthonormal and block-pure."""
+    Lx, Ly = 3, 3
+    peps, _, qpeps, W, qW = _lattice(Lx, Ly, 3, 6)
+    bundles = [[S.site_bundles(qpeps[r][c], qW[r][c]) for c in range(Ly)] for r in range(Lx)]
+    T, _ = B.first_row_boundary(peps[0], W[0])
+    qT = S.first_row_charges(bundles[0])
+    # Theta of row 1 at site 0 (trivial left environment): rows Dn_0, columns (t_0, R_0)
+    Th = B.form_theta(np.ones((1, 1, 1)), T[0], peps[1][0], W[1][0])
+    QD, QR = bundles[1][0][3], bundles[1][0][2]
+    rowq = -QD
+    colq = (qT[0][:, None, :] + QR[None, :, :]).reshape(-1, 2)
+    chi, prm = 3, B.RsvdParams(n_fit=0, oversample=1, power_iters=1)
+    ranks = []
+    for q in S._sectors(rowq, colq):
+        sv = np.linalg.svd(Th[np.ix_(np.all(rowq == q, axis=1), np.all(colq == q, axis=1))], compute_uv=False)
+        ranks.append(int((sv > 1e-12 * sv.max()).sum()))
+    assert max(ranks) > chi + prm.oversample          # a sector is sketched, not solved exactly
+    om = lambda k: np.random.default_rng(1).standard_normal((Th.shape[1], k))
+    U, s, Vt, qk, _ = S.sector_rsvd(lambda X: Th @ X, lambda Y: Th.T @ Y, rowq, colq, chi, prm, om)
+    exact = np.linalg.svd(Th, compute_uv=False)[:len(s)]
+    assert np.all(np.sort(s)[::-1] <= exact * (1 + 1e-12))
+    live = s > 1e-12 * s.max()
+    assert live.any()
+    assert np.allclose(U[:, live].T @ U[:, live], np.eye(live.sum()), atol=1e-12)
+    assert np.allclose(Vt[live] @ Vt[live].T, np.eye(live.sum()), atol=1e-12)
+    for m in range(len(s)):
+        assert np.all(U[~np.all(rowq == qk[m], axis=1), m] == 0)
+        assert np.all(Vt[m, ~np.all(colq == qk[m], axis=1)] == 0)
