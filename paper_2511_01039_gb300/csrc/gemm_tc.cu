@@ -23,15 +23,18 @@
 // of the tile's 128 B rows in its shared memory, and rank 0 issues M=256 MMAs that
 // read B from both. B's loads, split and MMA reads per SM halve (~88 KB per
 // k-block). Converters and epilogue warps of both CTAs arrive on rank 0's
-// barriers; MMA completion is signalled to both CTAs by a multicast commit.
+// barriers; MMA completion is signalled to both CTAs by a multicast commit. Each
+// pair CTA has two sets of A converters taking alternate k-blocks.
 //
 // Accumulation: the tensor cores' FP32 accumulation over long K loses far more
 // than round-to-nearest FP32 (measured ~1e-5 relative at K = 2048, ~1e-3 at
 // K = 1e5). K is therefore cut into chunks of KCH_BLOCKS * BK = 256 terms; each
 // chunk accumulates in a fresh TMEM accumulator and the epilogue warps add it to
-// a running FP32 sum in TMEM (the MMAs of the next chunk wait for that drain;
-// tiles of a single chunk alternate two accumulators instead, so a tile's MMAs
-// overlap the previous tile's drain). Few output tiles are additionally split
+// a running FP32 sum. A single CTA keeps that sum in TMEM (the MMAs of the next
+// chunk wait for the drain; tiles of a single chunk alternate two accumulators
+// instead, so a tile's MMAs overlap the previous tile's drain); a pair CTA keeps
+// it in shared memory and always alternates two TMEM accumulators, so no chunk
+// waits for a drain. Few output tiles are additionally split
 // over K across CTAs, with the partials summed in FP64. Output blocks whose contiguous index is n
 // pass through shared memory so that every store instruction is coalesced.
 //
@@ -207,11 +210,12 @@ struct TcArgs {
 // and store hi and lo straight into a TMEM slot with tcgen05.st; only B's hi/lo
 // tiles stay in shared memory, so the MMAs read B alone from shared memory and the
 // A split costs no shared-memory writes. TMEM columns: [0,128) a chunk
-// accumulator; [128,256) a second one when every tile is a single chunk (tiles
-// alternate, so the next tile's MMAs overlap the drain), else the running FP32
-// sum; [256,512) four A slots of 32 hi + 32 lo columns, one per stage. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane quarter =
-// warp % 4), 6..7 and 12..15 B converters, 8..11 epilogue, 16 barrier waiter
-// for the MMA warp.
+// accumulator; [128,256) a second one when every tile is a single chunk or the
+// CTA is part of a pair (chunks alternate, so the next chunk's MMAs overlap the
+// drain), else the running FP32 sum; [256,512) four A slots of 32 hi + 32 lo
+// columns, one per stage. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane
+// quarter = warp % 4), 6..7 and 12..15 B converters (in a pair CTA 12..15 are a
+// second set of A converters), 8..11 epilogue, 16 barrier waiter for the MMA warp.
 constexpr int P_THREADS = 544;
 constexpr int T_STAGES = 4;
 // Shared memory: the stage ring (A fp32 | B hi (in place) | B lo; a pair CTA holds
