@@ -75,7 +75,7 @@ typedef struct {
   int32_t chi;           /* boundary bond dimension, >= 1 */
   fpeps_precision prec;  /* contraction arithmetic */
   uint64_t seed;         /* key of the Gaussian sketches */
-  int32_t symmetry;      /* 0 = dense (1 = U(1)xU(1) block-sparse: not built) */
+  int32_t symmetry;      /* 0 = dense, 1 = U(1) x U(1) charge sectors (zip-up compression only) */
   int32_t n_envs;        /* 1 (batched environments: not built) */
 } fpeps_config;
 
@@ -104,15 +104,27 @@ typedef struct fpeps_env fpeps_env;
  *              [Dl,Du,Dr,Dd,p] C-contiguous, edge legs 1), element type dtype_in.
  *   pepo_dev   device buffer with all operator PEPO sites [wl,wu,wr,wd,p,p'],
  *              or NULL for none (then only fpeps_contract_norm is available).
- *   charges_host  must be NULL (block-sparse mode is not built).
+ *   charges_host  NULL when cfg->symmetry == 0; else host int32 charges
+ *              (N_up, N_dn) of every leg index (Sec. V: U(1) x U(1) symmetric
+ *              tensors): for each PEPS site in row-major order its legs
+ *              l, u, r, d, each as dim pairs; then, if pepo_dev is given, the
+ *              same for every PEPO site (dims w or 1 at the edges). The caller
+ *              guarantees the tensors conserve them: PEPS q_l+q_u+q_p =
+ *              q_r+q_d+f_site, PEPO q_l+q_u+q_p = q_r+q_d+q_p'. The buffer is read
+ *              during the call. With symmetry 1 every compression runs the rSVD
+ *              sector by sector in the charge of the cut bond, with one global
+ *              truncation to chi; only the zip-up pass is built (n_fit must be 0,
+ *              else FPEPS_ERR_UNSUPPORTED), and a boundary imported by
+ *              fpeps_import_boundary carries no charges (FPEPS_ERR_STATE).
  *   dtype_in   0 = float64, 1 = float32.
  *   cuda_stream   cudaStream_t on which all work is enqueued (NULL = default).
  *   alloc      device allocator or NULL.
  * The inputs are copied (and converted to the compute precision) before the
  * call returns; the caller keeps ownership of its buffers.
  * Errors: FPEPS_ERR_ARG (bad sizes/pointers), FPEPS_ERR_OOM, FPEPS_ERR_CUDA,
- * FPEPS_ERR_UNSUPPORTED (symmetry != 0, n_envs != 1, or prec == FPEPS_BF16X3,
- * whose kernels are not built). */
+ * FPEPS_ERR_UNSUPPORTED (n_envs != 1, or prec == FPEPS_BF16X3, whose kernels
+ * are not built); FPEPS_ERR_ARG also when symmetry is not 0 or 1 or charges_host
+ * does not match it. */
 fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, const void* pepo_dev,
                               const int32_t* charges_host, int32_t dtype_in, void* cuda_stream,
                               const fpeps_allocator* alloc, fpeps_env** out);

@@ -233,7 +233,9 @@ fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, con
   if (c.prec < FPEPS_F64 || c.prec > FPEPS_BF16X3) return FPEPS_ERR_ARG;
   if (dtype_in != 0 && dtype_in != 1) return FPEPS_ERR_ARG;
   if (c.Ly > 4096 || c.Lx > 4096 || c.D > 64 || c.p > 64 || c.w > 64) return FPEPS_ERR_ARG;
-  if (c.symmetry != 0 || c.n_envs != 1 || charges_host) return FPEPS_ERR_UNSUPPORTED;
+  if (c.n_envs != 1) return FPEPS_ERR_UNSUPPORTED;
+  if (c.symmetry != 0 && c.symmetry != 1) return FPEPS_ERR_ARG;
+  if ((c.symmetry == 1) != (charges_host != nullptr)) return FPEPS_ERR_ARG;
   if (c.prec == FPEPS_BF16X3) return FPEPS_ERR_UNSUPPORTED;   // 3xBF16 kernels are not built
   fpeps_env* env = new (std::nothrow) fpeps_env();
   if (!env) return FPEPS_ERR_OOM;
@@ -267,6 +269,40 @@ fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, con
         h0.offW = offI;
         offI += (size_t)c.p * c.p;
       }
+    if (c.symmetry == 1) {
+      // leg charges -> bundle charges Q = q_ket - q_pepo - q_bra per (ket, PEPO, bra)
+      // bundle index, bra fastest; the identity PEPO of layer 0 carries no charge
+      const size_t n = (size_t)c.Lx * c.Ly;
+      const int32_t* q = charges_host;
+      std::vector<const int32_t*> qa(n * 4), qw(n * 4, nullptr);
+      for (size_t i = 0; i < n; ++i)
+        for (int l = 0; l < 4; ++l) {
+          qa[i * 4 + l] = q;
+          q += 2 * env->sites[1][i].dA[l];
+        }
+      if (pepo_dev)
+        for (size_t i = 0; i < n; ++i)
+          for (int l = 0; l < 4; ++l) {
+            qw[i * 4 + l] = q;
+            q += 2 * env->sites[1][i].dW[l];
+          }
+      for (int layer = 0; layer < 2; ++layer)
+        for (size_t i = 0; i < n; ++i) {
+          auto& h = env->sites[layer][i];
+          for (int l = 0; l < 4; ++l) {
+            const int dk = h.dA[l], dw = h.dW[l];
+            const int32_t* qk = qa[i * 4 + l];
+            const int32_t* qp = layer == 1 ? qw[i * 4 + l] : nullptr;
+            std::vector<int32_t> v((size_t)2 * dk * dw * dk);
+            for (int x = 0; x < dk; ++x)
+              for (int y = 0; y < dw; ++y)
+                for (int z = 0; z < dk; ++z)
+                  for (int t = 0; t < 2; ++t)
+                    v[2 * (((size_t)x * dw + y) * dk + z) + t] = qk[2 * x + t] - (qp ? qp[2 * y + t] : 0) - qk[2 * z + t];
+            h.qB[l] = std::move(v);
+          }
+        }
+    }
     FP_CUDA(cudaMallocHost((void**)&env->h_info, 16 * sizeof(int)));
     FP_CUDA(cudaMallocHost((void**)&env->h_scal, 16 * sizeof(double)));
     env->d_info = (int*)env->al.get(16 * sizeof(int));
@@ -438,6 +474,7 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
     if (!on_dev) FP_CUDA(cudaStreamSynchronize(env->stream));
     env->tb = tb;
     env->tphys = ph;
+    env->qT.clear();   // a checkpoint carries no charges
     env->layer = layer;
     env->next_row = next_row;
     env->state = fpeps::RowState::Ready;

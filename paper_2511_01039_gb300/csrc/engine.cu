@@ -17,9 +17,11 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <functional>
+#include <map>
 
 #include "env.cuh"
 
@@ -35,6 +37,12 @@ template <class T>
 void set_identity(cudaStream_t s, T* X, int64_t m, int n);
 template <class T>
 void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst);
+template <class T>
+void gather_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx, int64_t n, int64_t k, T* dst,
+                 int64_t ldd);
+template <class T>
+void scatter_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx, int64_t n, int64_t k, T* dst,
+                  int64_t ldd);
 
 namespace {
 
@@ -588,6 +596,10 @@ struct Engine : EngineBase {
     e->tb = tb;
     e->tphys = ph;
     e->log_scale += log_s;
+    if (e->cfg.symmetry == 1) {   // bond t_c of the exact row-0 boundary is the R bundle of site c
+      e->qT.assign(Ly + 1, std::vector<int32_t>{0, 0});
+      for (int c = 0; c < Ly - 1; ++c) e->qT[c + 1] = e->sites[e->layer][row * Ly + c].qB[2];
+    }
   }
 
   void close_row(fpeps_env* e, int row) override {
@@ -650,6 +662,14 @@ struct Engine : EngineBase {
     e->spectra.zip.assign(Ly, {});
     e->spectra.fit.assign(Ly, {});
 
+    const bool sym = e->cfg.symmetry == 1;
+    if (sym) {
+      FP_CHECK(prm.n_fit == 0 || Ly == 1, FPEPS_ERR_UNSUPPORTED,
+               "charge sectors: only the zip-up compression is built (n_fit must be 0)");
+      FP_CHECK((int)e->qT.size() == Ly + 1, FPEPS_ERR_STATE, "charge sectors: the boundary carries no charges");
+    }
+    std::vector<std::vector<int32_t>> qnew(Ly + 1, std::vector<int32_t>{0, 0});
+    std::vector<int32_t> qa{0, 0};               // charges of the new bond a_{c-1}
     Arena rowmem = arena();                      // lives for the whole row
     std::vector<T*> Nvec(Ly, nullptr);           // zip-up isometries as vectors [chi][Dn][a]
     std::vector<int> abond(Ly + 1, 1);           // new bonds
@@ -665,6 +685,161 @@ struct Engine : EngineBase {
       Site st = make_site(ar, row, c, true, false);
       const int a = EL[c].a;
       const int64_t rows = (int64_t)a * st.bD, cols = (int64_t)st.tp * st.bR;
+      if (sym) {
+        // Theta_c is block diagonal in the charge of the cut bond: rows (Dn, a) carry
+        // q_a - Q_Dn, columns (R, t') carry q_t' + Q_R. rSVD per sector (sketch = the
+        // dense Omega's rows of the sector's columns), one global truncation to chi.
+        const SiteHost& hs = e->sites[e->layer][row * Ly + c];
+        const std::vector<int32_t>& QD = hs.qB[3];
+        const std::vector<int32_t>& QR = hs.qB[2];
+        const std::vector<int32_t>& qt = e->qT[c + 1];
+        FP_CHECK((int64_t)QD.size() == 2 * st.bD && (int64_t)QR.size() == 2 * st.bR &&
+                     (int64_t)qt.size() == 2 * st.tp && (int64_t)qa.size() == 2 * a,
+                 FPEPS_ERR_STATE, "charge sectors: charge lists do not match the bonds");
+        using Key = std::pair<int32_t, int32_t>;
+        std::map<Key, std::vector<int64_t>> rmap, cmap;
+        for (int64_t d = 0; d < st.bD; ++d)
+          for (int64_t ai = 0; ai < a; ++ai)
+            rmap[{qa[2 * ai] - QD[2 * d], qa[2 * ai + 1] - QD[2 * d + 1]}].push_back(d * a + ai);
+        for (int64_t R = 0; R < st.bR; ++R)
+          for (int64_t tq = 0; tq < st.tp; ++tq)
+            cmap[{qt[2 * tq] + QR[2 * R], qt[2 * tq + 1] + QR[2 * R + 1]}].push_back(R * st.tp + tq);
+        struct Sec {
+          Key q;
+          std::vector<int64_t> ri, ci;
+          int64_t *d_ri = nullptr, *d_ci = nullptr;
+          int cap = 0, k = 0;
+          T *L = nullptr, *Rv = nullptr;
+          std::vector<double> sig;
+        };
+        std::vector<Sec> secs;
+        for (auto& kv : rmap) {
+          auto it = cmap.find(kv.first);
+          if (it == cmap.end()) continue;
+          Sec x;
+          x.q = kv.first;
+          x.ri = kv.second;
+          x.ci = it->second;
+          const int64_t rank = std::min<int64_t>((int64_t)x.ri.size(), (int64_t)x.ci.size());
+          x.cap = (int)std::min<int64_t>(chi, rank);
+          if (x.cap == 0) continue;
+          x.k = prm.exact_svd ? (int)rank : (int)std::min<int64_t>((int64_t)x.cap + prm.oversample, rank);
+          secs.push_back(std::move(x));
+        }
+        FP_CHECK(!secs.empty(), FPEPS_ERR_NUMERIC, "charge sectors: rows and columns share no charge");
+        int kmax = 0;
+        for (auto& x : secs) kmax = std::max(kmax, x.k);
+        T* omega = ar.get_n<T>(cols * kmax);
+        int64_t perm[2] = {st.bR, st.tp};
+        gaussian_sketch<T>(s, omega, cols, kmax, cols, perm, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c, w3);
+        T* fullc = ar.get_n<T>(cols * kmax);
+        T* fullr = ar.get_n<T>(rows * kmax);
+        Env3 elc = EL[c];
+        double tot = 0.0;
+        for (auto& x : secs) {
+          const int64_t nr = (int64_t)x.ri.size(), nc = (int64_t)x.ci.size();
+          x.d_ri = ar.get_n<int64_t>(nr);
+          x.d_ci = ar.get_n<int64_t>(nc);
+          FP_CUDA(cudaMemcpyAsync(x.d_ri, x.ri.data(), sizeof(int64_t) * nr, cudaMemcpyHostToDevice, s));
+          FP_CUDA(cudaMemcpyAsync(x.d_ci, x.ci.data(), sizeof(int64_t) * nc, cudaMemcpyHostToDevice, s));
+          T* om = ar.get_n<T>(nc * x.k);
+          gather_rows<T>(s, omega, cols, x.d_ci, nc, x.k, om, nc);
+          const int64_t* dri = x.d_ri;
+          const int64_t* dci = x.d_ci;
+          Lin A{nr, nc,
+                [&, dri, dci, nr, nc](const T* X, T* Y, int64_t kk) {
+                  FP_CUDA(cudaMemsetAsync(fullc, 0, sizeof(T) * cols * kk, s));
+                  scatter_rows<T>(s, X, nc, dci, nc, kk, fullc, cols);
+                  theta(st, elc, fullc, fullr, kk);
+                  gather_rows<T>(s, fullr, rows, dri, nr, kk, Y, nr);
+                },
+                [&, dri, dci, nr, nc](const T* Y, T* Z, int64_t kk) {
+                  FP_CUDA(cudaMemsetAsync(fullr, 0, sizeof(T) * rows * kk, s));
+                  scatter_rows<T>(s, Y, nr, dri, nr, kk, fullr, rows);
+                  theta_t(st, elc, fullr, fullc, kk);
+                  gather_rows<T>(s, fullc, cols, dci, nc, kk, Z, nc);
+                }};
+          RsvdOut r = rsvd(ar, A, om, x.k, prm.power_iters);
+          T* Ut = ar.get_n<T>((int64_t)x.k * x.k);
+          convert_f64<T>(s, r.U, Ut, (int64_t)x.k * x.k);
+          x.L = ar.get_n<T>(nr * x.k);
+          mm_right(nr, x.k, x.k, r.Q, nr, Ut, x.k, x.L, nr);
+          x.Rv = r.QbW;
+          x.sig = r.sigma;
+          for (double v : r.sigma) tot += v * v;
+        }
+        // global truncation: the chi_c largest over the sectors' offers (ties: sector
+        // order, then index); kept triplets ordered by sector, then value
+        struct Cand {
+          double v;
+          int n, j;
+        };
+        std::vector<Cand> cand;
+        int64_t capsum = 0;
+        for (int n = 0; n < (int)secs.size(); ++n) {
+          capsum += secs[n].cap;
+          for (int j = 0; j < secs[n].cap; ++j) cand.push_back({-secs[n].sig[j], n, j});
+        }
+        const int chi_c = (int)std::min<int64_t>(chi, capsum);
+        auto lex = [](const Cand& x, const Cand& y) {
+          return x.v != y.v ? x.v < y.v : (x.n != y.n ? x.n < y.n : x.j < y.j);
+        };
+        std::sort(cand.begin(), cand.end(), lex);
+        cand.resize(chi_c);
+        std::sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) {
+          return x.n != y.n ? x.n < y.n : x.j < y.j;
+        });
+        T* N = rowmem.get_n<T>(rows * chi_c);
+        T* elv = rowmem.get_n<T>(cols * chi_c);
+        FP_CUDA(cudaMemsetAsync(N, 0, sizeof(T) * rows * chi_c, s));
+        FP_CUDA(cudaMemsetAsync(elv, 0, sizeof(T) * cols * chi_c, s));
+        std::vector<double> sv(chi_c), alive(chi_c);
+        std::vector<int32_t> qk(2 * (size_t)chi_c);
+        double kept2 = 0.0;
+        for (int m = 0; m < chi_c; ++m) {
+          const Sec& x = secs[cand[m].n];
+          const int j = cand[m].j;
+          const int64_t nr = (int64_t)x.ri.size(), nc = (int64_t)x.ci.size();
+          scatter_rows<T>(s, x.L + (int64_t)j * nr, nr, x.d_ri, nr, 1, N + (int64_t)m * rows, rows);
+          scatter_rows<T>(s, x.Rv + (int64_t)j * nc, nc, x.d_ci, nc, 1, elv + (int64_t)m * cols, cols);
+          sv[m] = x.sig[j];
+          kept2 += sv[m] * sv[m];
+          alive[m] = (tot > 0 && sv[m] * sv[m] > 1e-30 * tot) ? 1.0 : 0.0;
+          qk[2 * m] = x.q.first;
+          qk[2 * m + 1] = x.q.second;
+        }
+        double* d_alive = ar.get_n<double>(chi_c);
+        FP_CUDA(cudaMemcpyAsync(d_alive, alive.data(), sizeof(double) * chi_c, cudaMemcpyHostToDevice, s));
+        scale_cols<T>(s, N, rows, chi_c, rows, d_alive);
+        // sign gauge and remainder, as in the dense zip-up
+        double* sgn = ar.get_n<double>(chi_c);
+        T* gw = ar.get_n<T>(rows);
+        int64_t gperm[2] = {st.bD, a};
+        gaussian_sketch<T>(s, gw, rows, 1, rows, gperm, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16),
+                           w3);
+        col_signs<T>(s, N, rows, chi_c, rows, gw, sgn);
+        scale_cols<T>(s, N, rows, chi_c, rows, sgn);
+        double* sc = ar.get_n<double>(chi_c);
+        double* sgd = ar.get_n<double>(chi_c);
+        FP_CUDA(cudaMemcpyAsync(sgd, sv.data(), sizeof(double) * chi_c, cudaMemcpyHostToDevice, s));
+        mul_vec(s, sgd, sgn, sc, chi_c);
+        scale_cols<T>(s, elv, cols, chi_c, cols, sc);
+        double nrm = host_norm(elv, cols * chi_c);
+        FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "zip-up remainder vanished");
+        scale_by_inv<T>(s, elv, cols * chi_c, e->d_scal);
+        log_s += std::log(nrm);
+        trunc_den += tot;
+        trunc_num += std::max(0.0, tot - kept2);
+        e->spectra.zip[c] = sv;
+        qa = qk;
+        qnew[c + 1] = qk;
+        Nvec[c] = N;
+        abond[c + 1] = chi_c;
+        ELvec[c + 1] = elv;
+        EL[c + 1] = env_from_vectors(rowmem, elv, chi_c, st.bR, st.tp);
+        FP_CUDA(cudaStreamSynchronize(s));
+        continue;
+      }
       const int chi_c = (int)std::min<int64_t>({(int64_t)chi, rows, cols});
       const int k = prm.exact_svd ? (int)std::min(rows, cols)
                                   : (int)std::min<int64_t>({(int64_t)chi_c + prm.oversample, rows, cols});
@@ -761,6 +936,7 @@ struct Engine : EngineBase {
     e->tb = tb_new;
     e->tphys = ph_new;
     e->log_scale += log_row;
+    if (sym) e->qT = qnew;
     FP_CUDA(cudaEventRecord(ev1, s));
     FP_CUDA(cudaEventSynchronize(ev1));
     float ms = 0;

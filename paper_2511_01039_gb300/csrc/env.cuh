@@ -18,6 +18,9 @@ struct SiteHost {
   size_t offA = 0, offW = 0;   // element offsets into the packed device buffers
   // channels of the PEPO site in (l,u,r,d) order
   std::vector<int> ch;   // 4 ints per channel
+  // block-sparse mode: U(1) x U(1) charges (N_up, N_dn) of the (ket, PEPO, bra)
+  // bundles of legs l, u, r, d, bra fastest: Q = q_ket - q_pepo - q_bra
+  std::vector<int32_t> qB[4];
 };
 
 // Sandwich data of one site for the four orientations (device memory, per layer).
@@ -53,6 +56,7 @@ struct fpeps_env {
   std::vector<void*> T;
   std::vector<int> tb;      // Ly+1 bond dims
   std::vector<int> tphys;   // Ly phys (bundle) dims
+  std::vector<std::vector<int32_t>> qT;   // block-sparse mode: charges of the Ly+1 bonds (pairs)
   double log_scale = 0.0;   // ln of the scale taken out of the boundary so far
   int next_row = 0;
   int layer = 0;

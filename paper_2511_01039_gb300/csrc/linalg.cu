@@ -909,6 +909,41 @@ void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst) {
   FP_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, s));
 }
 
+// Row selection within every column of a column-major block (charge sectors of
+// the block-sparse mode): gather dst[i + j ldd] = src[idx[i] + j lds], scatter
+// dst[idx[i] + j ldd] = src[i + j lds], for i < n, j < k. idx holds valid rows of
+// the indexed side (checked on the host when the lists are built).
+template <class T>
+__global__ void k_gather_rows(const T* __restrict__ src, int64_t lds, const int64_t* __restrict__ idx, int64_t n,
+                              int64_t k, T* __restrict__ dst, int64_t ldd) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e % n;
+    dst[j * ldd + i] = src[j * lds + idx[i]];
+  }
+}
+template <class T>
+__global__ void k_scatter_rows(const T* __restrict__ src, int64_t lds, const int64_t* __restrict__ idx, int64_t n,
+                               int64_t k, T* __restrict__ dst, int64_t ldd) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e % n;
+    dst[j * ldd + idx[i]] = src[j * lds + i];
+  }
+}
+template <class T>
+void gather_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx, int64_t n, int64_t k, T* dst,
+                 int64_t ldd) {
+  if (n * k == 0) return;
+  k_gather_rows<T><<<grid_for(n * k), 256, 0, s>>>(src, lds, idx, n, k, dst, ldd);
+  FP_LAUNCH();
+}
+template <class T>
+void scatter_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx, int64_t n, int64_t k, T* dst,
+                  int64_t ldd) {
+  if (n * k == 0) return;
+  k_scatter_rows<T><<<grid_for(n * k), 256, 0, s>>>(src, lds, idx, n, k, dst, ldd);
+  FP_LAUNCH();
+}
+
 #define INST(T)                                                                                              \
   template void gaussian_sketch<T>(cudaStream_t, T*, int64_t, int64_t, int64_t, const int64_t*, uint64_t,    \
                                    uint64_t, uint64_t, uint64_t);                                            \
@@ -926,7 +961,9 @@ void copy_cols(cudaStream_t s, const T* src, int64_t m, int n, T* dst) {
   template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, const T*, double*);                         \
   template void scale_cols<T>(cudaStream_t, T*, int64_t, int, int64_t, const double*);                        \
   template void set_identity<T>(cudaStream_t, T*, int64_t, int);                                              \
-  template void copy_cols<T>(cudaStream_t, const T*, int64_t, int, T*);
+  template void copy_cols<T>(cudaStream_t, const T*, int64_t, int, T*);                                      \
+  template void gather_rows<T>(cudaStream_t, const T*, int64_t, const int64_t*, int64_t, int64_t, T*, int64_t);   \
+  template void scatter_rows<T>(cudaStream_t, const T*, int64_t, const int64_t*, int64_t, int64_t, T*, int64_t);
 INST(float)
 INST(double)
 template void fill<int>(cudaStream_t, int*, int64_t, int);

@@ -133,13 +133,21 @@ class TorchAllocator:
 
 
 # ------------------------------------------------------------------ same-name wrappers
-def fpeps_env_create(cfg: fpeps_config, peps, pepo, dtype_in: int, stream_handle: int, allocator=None):
-    """peps/pepo: device pointers (int) or torch tensors; returns the env handle (c_void_p)."""
+def fpeps_env_create(cfg: fpeps_config, peps, pepo, dtype_in: int, stream_handle: int, allocator=None,
+                     charges=None):
+    """peps/pepo: device pointers (int) or torch tensors; charges: None or a contiguous
+    int32 numpy array in the layout of the C header (cfg.symmetry must be 1); returns
+    the env handle (c_void_p)."""
+    import numpy as np
     out = C.c_void_p()
     pp = peps.data_ptr() if hasattr(peps, "data_ptr") else peps
     wp = (pepo.data_ptr() if hasattr(pepo, "data_ptr") else pepo) if pepo is not None else None
     al = C.byref(allocator.struct) if allocator is not None else None
-    st = lib().fpeps_env_create(C.byref(cfg), pp, wp, None, dtype_in, stream_handle, al, C.byref(out))
+    qp = None
+    if charges is not None:
+        charges = np.ascontiguousarray(charges, dtype=np.int32)
+        qp = charges.ctypes.data
+    st = lib().fpeps_env_create(C.byref(cfg), pp, wp, qp, dtype_in, stream_handle, al, C.byref(out))
     _check(None, st)
     return out
 
@@ -287,7 +295,8 @@ class Env:
     to the device once; ``prec`` one of 'f64', 'f32', 'tf32x3', 'bf16x3'.
     """
 
-    def __init__(self, peps, pepo, *, D, p, w, chi, prec="f64", seed=0, stream=None, use_torch_allocator=True):
+    def __init__(self, peps, pepo, *, D, p, w, chi, prec="f64", seed=0, stream=None, use_torch_allocator=True,
+                 charges=None):
         import numpy as np
         import torch
         self.torch = torch
@@ -299,11 +308,11 @@ class Env:
         wk = None
         if pepo is not None:
             wk = torch.cat([torch.as_tensor(np.asarray(t), dtype=dt).reshape(-1) for row in pepo for t in row]).to(self.dev)
-        self.cfg = fpeps_config(Lx, Ly, D, p, w, chi, PRECISIONS[prec], seed, 0, 1)
+        self.cfg = fpeps_config(Lx, Ly, D, p, w, chi, PRECISIONS[prec], seed, 1 if charges is not None else 0, 1)
         self.elem = 8 if prec == "f64" else 4
         self.alloc = TorchAllocator(self.dev) if use_torch_allocator else None
         torch.cuda.synchronize(self.dev)
-        self.h = fpeps_env_create(self.cfg, pk, wk, 0, self.stream.cuda_stream, self.alloc)
+        self.h = fpeps_env_create(self.cfg, pk, wk, 0, self.stream.cuda_stream, self.alloc, charges)
         del pk, wk
 
     def close(self):
@@ -326,6 +335,16 @@ class Env:
     def apply_theta(self, c, el, x, dn):
         """One Theta_c application of the staged row (diagnostic): el [a,t,L], x [k,t',R] -> y [k,a,dn]."""
         return fpeps_apply_theta(self.h, c, el, x, dn, self.elem)
+
+
+def pack_charges(qpeps, qpepo=None):
+    """Leg charges in the layout of fpeps_env_create: qpeps[r][c] (and qpepo[r][c])
+    = (q_l, q_u, q_r, q_d), each an (dim, 2) integer array; PEPS sites first."""
+    import numpy as np
+    parts = [np.asarray(q, dtype=np.int32).reshape(-1) for row in qpeps for site in row for q in site]
+    if qpepo is not None:
+        parts += [np.asarray(q, dtype=np.int32).reshape(-1) for row in qpepo for site in row for q in site]
+    return np.concatenate(parts)
 
 
 def params(oversample=10, power_iters=2, chi_tilde=0, n_fit=1, exact_svd=0) -> fpeps_rsvd_params:

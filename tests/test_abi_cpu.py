@@ -47,7 +47,17 @@ def test_create_rejects_bad_arguments_without_gpu(built):
     cfg = fpeps.fpeps_config(0, 3, 2, 4, 1, 8, 0, 0, 0, 1)
     st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
     assert st == 1 and not out.value
-    cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 1, 1)       # block-sparse not built
+    cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 1, 1)       # charge sectors without charges
+    st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
+    assert st == 1
+    q = (ctypes.c_int32 * 4)()
+    cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 0, 1)       # charges without charge sectors
+    st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, q, 0, None, None, ctypes.byref(out))
+    assert st == 1
+    cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 2, 1)       # unknown symmetry
+    st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
+    assert st == 1
+    cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 0, 2)       # batched environments not built
     st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
     assert st == 7
     cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 3, 0, 0, 1)       # 3xBF16 not built
