@@ -75,7 +75,7 @@ typedef struct {
   int32_t chi;           /* boundary bond dimension, >= 1 */
   fpeps_precision prec;  /* contraction arithmetic */
   uint64_t seed;         /* key of the Gaussian sketches */
-  int32_t symmetry;      /* 0 = dense, 1 = U(1) x U(1) charge sectors (zip-up compression only) */
+  int32_t symmetry;      /* 0 = dense, 1 = U(1) x U(1) charge sectors */
   int32_t n_envs;        /* 1 (batched environments: not built) */
 } fpeps_config;
 
@@ -111,11 +111,11 @@ typedef struct fpeps_env fpeps_env;
  *              same for every PEPO site (dims w or 1 at the edges). The caller
  *              guarantees the tensors conserve them: PEPS q_l+q_u+q_p =
  *              q_r+q_d+f_site, PEPO q_l+q_u+q_p = q_r+q_d+q_p'. The buffer is read
- *              during the call. With symmetry 1 every compression runs the rSVD
- *              sector by sector in the charge of the cut bond, with one global
- *              truncation to chi; only the zip-up pass is built (n_fit must be 0,
- *              else FPEPS_ERR_UNSUPPORTED), and a boundary imported by
- *              fpeps_import_boundary carries no charges (FPEPS_ERR_STATE).
+ *              during the call. With symmetry 1 every factorisation of the
+ *              compression (zip-up rSVD, CBE rSVD, SVD of the fitted tensor) runs
+ *              sector by sector in the charge of the bond it cuts, with one global
+ *              truncation; a boundary imported by fpeps_import_boundary carries
+ *              no charges (compression then returns FPEPS_ERR_STATE).
  *   dtype_in   0 = float64, 1 = float32.
  *   cuda_stream   cudaStream_t on which all work is enqueued (NULL = default).
  *   alloc      device allocator or NULL.

@@ -43,6 +43,8 @@ void gather_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx, 
 template <class T>
 void scatter_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx, int64_t n, int64_t k, T* dst,
                   int64_t ldd);
+template <class T>
+void transpose_block(cudaStream_t s, const T* src, int64_t lds, int64_t rows, int64_t cols, T* dst, int64_t ldd);
 
 namespace {
 
@@ -664,8 +666,6 @@ struct Engine : EngineBase {
 
     const bool sym = e->cfg.symmetry == 1;
     if (sym) {
-      FP_CHECK(prm.n_fit == 0 || Ly == 1, FPEPS_ERR_UNSUPPORTED,
-               "charge sectors: only the zip-up compression is built (n_fit must be 0)");
       FP_CHECK((int)e->qT.size() == Ly + 1, FPEPS_ERR_STATE, "charge sectors: the boundary carries no charges");
     }
     std::vector<std::vector<int32_t>> qnew(Ly + 1, std::vector<int32_t>{0, 0});
@@ -928,7 +928,13 @@ struct Engine : EngineBase {
       }
     } else {
       if (prm.n_fit != 1) throw Error{FPEPS_ERR_UNSUPPORTED, "n_fit must be 0 or 1"};
-      log_row = fit(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem);
+      if (sym) {
+        std::vector<std::vector<int32_t>> qfit;
+        log_row = fit_sym(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem, qnew, qfit);
+        qnew = qfit;
+      } else {
+        log_row = fit(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem);
+      }
     }
     FP_CUDA(cudaStreamSynchronize(s));
     for (void* p : e->T) e->al.put(p);
@@ -1129,6 +1135,364 @@ struct Engine : EngineBase {
       a_prev = a2;
     }
     // site 0: M_0 [1][Dn_0][a_0]
+    const int Dn0 = bund(e->sites[e->layer][row * Ly], 3);
+    const int64_t n0 = (int64_t)Dn0 * a_c;
+    double nrm = host_norm(M, n0);
+    FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "fit centre vanished");
+    T* N0 = (T*)e->al.get(sizeof(T) * n0);
+    FP_CUDA(cudaMemcpyAsync(N0, M, sizeof(T) * n0, cudaMemcpyDeviceToDevice, s));
+    scale_by_inv<T>(s, N0, n0, e->d_scal);
+    T_new[0] = N0;
+    tb_new[0] = 1;
+    tb_new[1] = a_c;
+    FP_CUDA(cudaStreamSynchronize(s));
+    return rs_M + std::log(nrm);
+  }
+
+  // ---------------------------------------------------------------- charge sectors: CBE fit
+  using QKey = std::pair<int32_t, int32_t>;
+  struct SecIdx {
+    QKey q;
+    std::vector<int64_t> ri, ci;
+    int64_t *d_ri = nullptr, *d_ci = nullptr;
+  };
+  // charges shared by the rows and the columns (pairs per index), ascending, with
+  // their index lists on the host and the device
+  std::vector<SecIdx> sectors_of(Arena& ar, const std::vector<int32_t>& rowq, const std::vector<int32_t>& colq) {
+    std::map<QKey, std::vector<int64_t>> rm, cm;
+    for (int64_t i = 0; i < (int64_t)rowq.size() / 2; ++i) rm[{rowq[2 * i], rowq[2 * i + 1]}].push_back(i);
+    for (int64_t i = 0; i < (int64_t)colq.size() / 2; ++i) cm[{colq[2 * i], colq[2 * i + 1]}].push_back(i);
+    std::vector<SecIdx> out;
+    for (auto& kv : rm) {
+      auto it = cm.find(kv.first);
+      if (it == cm.end()) continue;
+      SecIdx x;
+      x.q = kv.first;
+      x.ri = kv.second;
+      x.ci = it->second;
+      out.push_back(std::move(x));
+    }
+    for (auto& x : out) {
+      x.d_ri = ar.get_n<int64_t>((int64_t)x.ri.size());
+      x.d_ci = ar.get_n<int64_t>((int64_t)x.ci.size());
+      FP_CUDA(cudaMemcpyAsync(x.d_ri, x.ri.data(), sizeof(int64_t) * x.ri.size(), cudaMemcpyHostToDevice, s));
+      FP_CUDA(cudaMemcpyAsync(x.d_ci, x.ci.data(), sizeof(int64_t) * x.ci.size(), cudaMemcpyHostToDevice, s));
+    }
+    return out;
+  }
+  struct Pick {
+    double v;
+    int n, j;
+  };
+  // the `keep` largest values over the sectors' offers (ties: sector, then index),
+  // returned in sector order, then index
+  static std::vector<Pick> pick_global(std::vector<Pick> cand, int keep) {
+    std::sort(cand.begin(), cand.end(), [](const Pick& x, const Pick& y) {
+      return x.v != y.v ? x.v < y.v : (x.n != y.n ? x.n < y.n : x.j < y.j);
+    });
+    cand.resize(std::min<size_t>(cand.size(), (size_t)std::max(keep, 0)));
+    std::sort(cand.begin(), cand.end(), [](const Pick& x, const Pick& y) { return x.n != y.n ? x.n < y.n : x.j < y.j; });
+    return cand;
+  }
+
+  // Right-to-left CBE fit with every factorisation split by the charge of the bond
+  // a_{c-1} it straddles (the block-sparse form of fit(); see oracle/symmetric.py):
+  // the CBE rSVD per sector (a sector offers at most min(chi_tilde, rows_Q - n_Q(a),
+  // cols_Q - n_Q(V)) vectors; chi_tilde kept over all sectors), the SVD of the fitted
+  // tensor per sector (chi kept over all sectors). qzip: charges of the zip-up bonds;
+  // qout receives the charges of the fitted bonds.
+  double fit_sym(int row, const fpeps_rsvd_params& prm, std::vector<T*>& Nvec, std::vector<int>& abond,
+                 std::vector<Env3>& EL, T* Nlast, std::vector<void*>& T_new, std::vector<int>& tb_new, Arena& rowmem,
+                 const std::vector<std::vector<int32_t>>& qzip, std::vector<std::vector<int32_t>>& qout) {
+    (void)rowmem;
+    fpeps_env* e = env;
+    const int Ly = e->cfg.Ly;
+    const int chi = e->cfg.chi;
+    const int chi_t = prm.chi_tilde > 0 ? prm.chi_tilde : (chi + 9) / 10;
+    const uint64_t w3 = (uint64_t)row;
+    Arena mmem = arena();
+    int a_prev = abond[Ly - 1];
+    int a_c = 1;
+    const int64_t nlast = (int64_t)a_prev * bund(e->sites[e->layer][row * Ly + Ly - 1], 3);
+    T* M = mmem.get_n<T>(nlast);
+    FP_CUDA(cudaMemcpyAsync(M, Nlast, sizeof(T) * nlast, cudaMemcpyDeviceToDevice, s));
+    Arena ermem = arena();
+    Env3 ER = unit_env(ermem);
+    double rs = 0.0, rs_M = 0.0;
+    std::vector<int32_t> qright{0, 0};
+    qout.assign(Ly + 1, std::vector<int32_t>{0, 0});
+    for (int c = Ly - 1; c >= 1; --c) {
+      Arena ar = arena();
+      Site sc = make_site(ar, row, c, false, true);
+      Site sl = make_site(ar, row, c - 1, true, false);
+      const int Dn = sc.bD;
+      const int64_t cols_a = (int64_t)Dn * a_c;
+      const int a2 = EL[c - 1].a;
+      const int Dnl = sl.bD;
+      const int64_t rows_a = (int64_t)a2 * Dnl;
+      const int na = abond[c];
+      const std::vector<int32_t>& QD = e->sites[e->layer][row * Ly + c].qB[3];
+      const std::vector<int32_t>& QDl = e->sites[e->layer][row * Ly + c - 1].qB[3];
+      const std::vector<int32_t>& qa_prev = qzip[c];
+      const std::vector<int32_t>& qa_left = qzip[c - 1];
+      FP_CHECK((int64_t)QD.size() == 2 * (int64_t)Dn && (int64_t)qright.size() == 2 * (int64_t)a_c &&
+                   (int64_t)qa_prev.size() == 2 * (int64_t)a_prev && a_prev == na &&
+                   (int64_t)QDl.size() == 2 * (int64_t)Dnl && (int64_t)qa_left.size() == 2 * (int64_t)a2,
+               FPEPS_ERR_STATE, "charge sectors: charge lists do not match the bonds (fit)");
+      // columns (Dn_c, a_c), a_c fastest: Q_Dn + q_{a_c}; rows (Dn_{c-1}, a_{c-2}), a fastest: q_a - Q_Dn
+      std::vector<int32_t> colq(2 * cols_a), rowq(2 * rows_a);
+      for (int64_t d = 0; d < Dn; ++d)
+        for (int64_t x = 0; x < a_c; ++x)
+          for (int t = 0; t < 2; ++t) colq[2 * (d * a_c + x) + t] = QD[2 * d + t] + qright[2 * x + t];
+      for (int64_t d = 0; d < Dnl; ++d)
+        for (int64_t x = 0; x < a2; ++x)
+          for (int t = 0; t < 2; ++t) rowq[2 * (d * a2 + x) + t] = qa_left[2 * x + t] - QDl[2 * d + t];
+      // V^T = orth(M^T): rows of different sectors have disjoint supports, so the
+      // orthonormalisation keeps every vector in its sector
+      int a_eff;
+      T* VT;
+      std::vector<int32_t> qV;
+      if (a_prev >= cols_a) {
+        a_eff = (int)cols_a;
+        VT = ar.get_n<T>(cols_a * a_eff);
+        set_identity<T>(s, VT, cols_a, a_eff);
+        qV = colq;
+      } else {
+        a_eff = a_prev;
+        VT = ar.get_n<T>(cols_a * a_eff);
+        qr(M, cols_a, a_eff, VT, nullptr);
+        qV = qa_prev;
+      }
+      T* Nl = Nvec[c - 1];
+      Env3 elc = EL[c - 1];
+      Env3 erc = ER;
+      // CBE: sector offers
+      std::vector<SecIdx> cs = sectors_of(ar, rowq, colq);
+      auto count_q = [](const std::vector<int32_t>& q, const QKey& k) {
+        int64_t n = 0;
+        for (size_t i = 0; i + 1 < q.size(); i += 2) n += (q[i] == k.first && q[i + 1] == k.second);
+        return n;
+      };
+      std::vector<int64_t> capof(cs.size());
+      int64_t capsum = 0;
+      for (size_t n = 0; n < cs.size(); ++n) {
+        capof[n] = std::min<int64_t>({(int64_t)chi_t, (int64_t)cs[n].ri.size() - count_q(qa_prev, cs[n].q),
+                                      (int64_t)cs[n].ci.size() - count_q(qV, cs[n].q)});
+        capsum += std::max<int64_t>(0, capof[n]);
+      }
+      const int ct = (int)std::min<int64_t>(chi_t, capsum);
+      T* Vp;
+      int j;
+      std::vector<int32_t> qVp = qV;
+      if (ct > 0) {
+        std::vector<int> cap(cs.size()), kq(cs.size());
+        int kmax = 0;
+        for (size_t n = 0; n < cs.size(); ++n) {
+          const int64_t rank = std::min<int64_t>((int64_t)cs[n].ri.size(), (int64_t)cs[n].ci.size());
+          cap[n] = (int)std::max<int64_t>(0, std::min<int64_t>({(int64_t)ct, rank, capof[n]}));
+          kq[n] = cap[n] > 0 ? (int)std::min<int64_t>((int64_t)cap[n] + prm.oversample, rank) : 0;
+          kmax = std::max(kmax, kq[n]);
+        }
+        T* omega = ar.get_n<T>(cols_a * kmax);
+        gaussian_sketch<T>(s, omega, cols_a, kmax, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer,
+                           (uint64_t)c | (1ull << 16), w3);
+        T* tmpA = ar.get_n<T>(std::max<int64_t>(a_eff, na) * kmax);
+        T* Xp = ar.get_n<T>(std::max(cols_a, rows_a) * kmax);
+        T* Zm = ar.get_n<T>(((int64_t)sl.tp * sl.bR) * kmax);
+        T* fullc = ar.get_n<T>(cols_a * kmax);
+        T* fullr = ar.get_n<T>(rows_a * kmax);
+        Projector PR = projector(ar, VT, cols_a, a_eff);
+        Projector PL = projector(ar, Nl, rows_a, na);
+        auto a_fwd = [&](const T* X, T* Y, int64_t kk) {   // A = P_L^perp Theta2s P_R^perp
+          project_out(PR, X, Xp, kk, tmpA);
+          theta_r(sc, erc, Xp, Zm, kk);
+          theta(sl, elc, Zm, Y, kk);
+          project_out(PL, Y, Y, kk, tmpA);
+        };
+        auto a_bwd = [&](const T* Y, T* X, int64_t kk) {
+          FP_CUDA(cudaMemcpyAsync(Xp, Y, sizeof(T) * rows_a * kk, cudaMemcpyDeviceToDevice, s));
+          project_out(PL, Xp, Xp, kk, tmpA);
+          theta_t(sl, elc, Xp, Zm, kk);
+          theta_r_t(sc, erc, Zm, X, kk);
+          project_out(PR, X, X, kk, tmpA);
+        };
+        std::vector<T*> rv(cs.size(), nullptr);
+        std::vector<std::vector<double>> sig(cs.size());
+        std::vector<Pick> cand;
+        double tot = 0.0;
+        for (size_t n = 0; n < cs.size(); ++n) {
+          if (cap[n] == 0) continue;
+          const int64_t nr = (int64_t)cs[n].ri.size(), nc = (int64_t)cs[n].ci.size();
+          const int64_t* dri = cs[n].d_ri;
+          const int64_t* dci = cs[n].d_ci;
+          T* om = ar.get_n<T>(nc * kq[n]);
+          gather_rows<T>(s, omega, cols_a, dci, nc, kq[n], om, nc);
+          Lin A{nr, nc,
+                [&, dri, dci, nr, nc](const T* X, T* Y, int64_t kk) {
+                  FP_CUDA(cudaMemsetAsync(fullc, 0, sizeof(T) * cols_a * kk, s));
+                  scatter_rows<T>(s, X, nc, dci, nc, kk, fullc, cols_a);
+                  a_fwd(fullc, fullr, kk);
+                  gather_rows<T>(s, fullr, rows_a, dri, nr, kk, Y, nr);
+                },
+                [&, dri, dci, nr, nc](const T* Y, T* Z, int64_t kk) {
+                  FP_CUDA(cudaMemsetAsync(fullr, 0, sizeof(T) * rows_a * kk, s));
+                  scatter_rows<T>(s, Y, nr, dri, nr, kk, fullr, rows_a);
+                  a_bwd(fullr, fullc, kk);
+                  gather_rows<T>(s, fullc, cols_a, dci, nc, kk, Z, nc);
+                }};
+          RsvdOut r = rsvd(ar, A, om, kq[n], prm.power_iters);
+          rv[n] = r.QbW;
+          sig[n] = r.sigma;
+          for (double v : r.sigma) tot += v * v;
+          for (int jj = 0; jj < cap[n]; ++jj) cand.push_back({-r.sigma[jj], (int)n, jj});
+        }
+        std::vector<Pick> kept = pick_global(cand, ct);
+        j = a_eff + ct;
+        T* cat = ar.get_n<T>(cols_a * j);
+        FP_CUDA(cudaMemsetAsync(cat, 0, sizeof(T) * cols_a * j, s));
+        copy_cols<T>(s, VT, cols_a, a_eff, cat);
+        for (int m = 0; m < ct; ++m) {
+          const SecIdx& x = cs[kept[m].n];
+          const double v = sig[kept[m].n][kept[m].j];
+          const int64_t nc = (int64_t)x.ci.size();
+          if (tot > 0 && v * v > 1e-30 * tot)   // right vectors of null values are not determined: zero
+            scatter_rows<T>(s, rv[kept[m].n] + (int64_t)kept[m].j * nc, nc, x.d_ci, nc, 1,
+                            cat + cols_a * (int64_t)(a_eff + m), cols_a);
+          qVp.push_back(x.q.first);
+          qVp.push_back(x.q.second);
+        }
+        Vp = ar.get_n<T>(cols_a * j);
+        qr(cat, cols_a, j, Vp, nullptr);
+      } else {
+        j = a_eff;
+        Vp = VT;
+      }
+      // expanded right environment and the fitted tensor at c-1 (pattern 2(a))
+      const int64_t nER = (int64_t)sl.tp * sl.bR;
+      T* ERp = ar.get_n<T>(nER * j);
+      theta_r(sc, erc, Vp, ERp, j);
+      T* Mp = ar.get_n<T>(rows_a * j);
+      theta(sl, elc, ERp, Mp, j);
+      // SVD of M' per sector (rows: charge of a_{c-1} from the left, columns: of V')
+      std::vector<SecIdx> ms = sectors_of(ar, rowq, qVp);
+      std::vector<T*> Ls(ms.size()), Ws(ms.size());
+      std::vector<std::vector<double>> sv(ms.size());
+      std::vector<Pick> mc;
+      double mtot = 0.0;
+      int64_t rsum = 0;
+      T* Bj = ar.get_n<T>(rows_a * j);
+      for (size_t n = 0; n < ms.size(); ++n) {
+        const int64_t nr = (int64_t)ms[n].ri.size(), ncj = (int64_t)ms[n].ci.size();
+        const int rr = (int)std::min(nr, ncj);
+        gather_rows<T>(s, Mp, rows_a, ms[n].d_ri, nr, j, Bj, nr);        // nr x j
+        T* Bs = ar.get_n<T>(nr * ncj);
+        for (int64_t q = 0; q < ncj; ++q)
+          FP_CUDA(cudaMemcpyAsync(Bs + q * nr, Bj + ms[n].ci[q] * nr, sizeof(T) * nr, cudaMemcpyDeviceToDevice, s));
+        const bool tall = nr >= ncj;
+        const int64_t mm = tall ? nr : ncj;   // QR of the tall orientation
+        T* Bt = Bs;
+        if (!tall) {
+          Bt = ar.get_n<T>(ncj * nr);
+          transpose_block<T>(s, Bs, nr, nr, ncj, Bt, ncj);
+        }
+        T* Qm = ar.get_n<T>(mm * rr);
+        double* Rm = ar.get_n<double>((int64_t)rr * rr);
+        qr(Bt, mm, rr, Qm, Rm);
+        double* Uj = ar.get_n<double>((int64_t)rr * rr);
+        double* Vj = ar.get_n<double>((int64_t)rr * rr);
+        double* sg = ar.get_n<double>(rr);
+        int* order = ar.get_n<int>(rr);
+        {
+          Phase ph_(this, 2);
+          svd_jacobi_f64(s, Rm, rr, Uj, sg, Vj, order, e->d_info, ar.get(64));
+        }
+        FP_CHECK(read_info() == 0, FPEPS_ERR_NUMERIC, "Jacobi SVD did not converge (sector fit)");
+        double* Vs = ar.get_n<double>((int64_t)rr * rr);
+        gather_cols_f64(s, Vj, order, rr, Vs);
+        T* Wt = ar.get_n<T>((int64_t)rr * rr);
+        T* Urt = ar.get_n<T>((int64_t)rr * rr);
+        convert_f64<T>(s, Uj, Wt, (int64_t)rr * rr);
+        convert_f64<T>(s, Vs, Urt, (int64_t)rr * rr);
+        // tall: B = Q R, R = U_r S W^T -> left Q U_r (nr x rr), right W (ncj x rr);
+        // wide: B^T = Q R likewise -> left W (nr x rr), right Q U_r (ncj x rr)
+        T* QU = ar.get_n<T>(mm * rr);
+        mm_right(mm, rr, rr, Qm, mm, Urt, rr, QU, mm);
+        Ls[n] = tall ? QU : Wt;
+        Ws[n] = tall ? Wt : QU;
+        sv[n].resize(rr);
+        FP_CUDA(cudaMemcpyAsync(sv[n].data(), sg, sizeof(double) * rr, cudaMemcpyDeviceToHost, s));
+        FP_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < rr; ++q) {
+          mtot += sv[n][q] * sv[n][q];
+          mc.push_back({-sv[n][q], (int)n, q});
+        }
+        rsum += rr;
+      }
+      const int keep = (int)std::min<int64_t>(chi, rsum);
+      FP_CHECK(keep > 0, FPEPS_ERR_NUMERIC, "charge sectors: fitted tensor has no shared sector");
+      std::vector<Pick> mk = pick_global(mc, keep);
+      T* Wfull = ar.get_n<T>((int64_t)j * keep);
+      T* Ufull = ar.get_n<T>(rows_a * keep);
+      FP_CUDA(cudaMemsetAsync(Wfull, 0, sizeof(T) * j * keep, s));
+      FP_CUDA(cudaMemsetAsync(Ufull, 0, sizeof(T) * rows_a * keep, s));
+      std::vector<double> skeep(keep);
+      std::vector<int32_t> qk(2 * (size_t)keep);
+      for (int m = 0; m < keep; ++m) {
+        const SecIdx& x = ms[mk[m].n];
+        const int64_t nr = (int64_t)x.ri.size(), ncj = (int64_t)x.ci.size();
+        const int q = mk[m].j;
+        skeep[m] = sv[mk[m].n][q];
+        if (mtot > 0 && skeep[m] * skeep[m] > 1e-30 * mtot)
+          scatter_rows<T>(s, Ws[mk[m].n] + (int64_t)q * ncj, ncj, x.d_ci, ncj, 1, Wfull + (int64_t)m * j, j);
+        scatter_rows<T>(s, Ls[mk[m].n] + (int64_t)q * nr, nr, x.d_ri, nr, 1, Ufull + (int64_t)m * rows_a, rows_a);
+        qk[2 * m] = x.q.first;
+        qk[2 * m + 1] = x.q.second;
+      }
+      // new right isometry N_c^T = V' W  ->  [keep][Dn][a_c]
+      T* Nc = (T*)e->al.get(sizeof(T) * cols_a * keep);
+      mm_right(cols_a, keep, j, Vp, cols_a, Wfull, j, Nc, cols_a);
+      double* sgn = ar.get_n<double>(keep);
+      T* gw = ar.get_n<T>(cols_a);
+      gaussian_sketch<T>(s, gw, cols_a, 1, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16),
+                         w3);
+      col_signs<T>(s, Nc, cols_a, keep, cols_a, gw, sgn);
+      scale_cols<T>(s, Nc, cols_a, keep, cols_a, sgn);
+      T_new[c] = Nc;
+      tb_new[c] = keep;
+      tb_new[c + 1] = a_c;
+      double* sgd = ar.get_n<double>(keep);
+      FP_CUDA(cudaMemcpyAsync(sgd, skeep.data(), sizeof(double) * keep, cudaMemcpyHostToDevice, s));
+      double* scl = ar.get_n<double>(keep);
+      mul_vec(s, sgd, sgn, scl, keep);
+      scale_cols<T>(s, Ufull, rows_a, keep, rows_a, scl);
+      Arena mnew = arena();
+      T* Mnext = mnew.get_n<T>(rows_a * keep);
+      permute3<T>(s, Ufull, Mnext, keep, Dnl, a2, 2, 1, 0);
+      T* erv = ar.get_n<T>(nER * keep);
+      mm_right(nER, keep, j, ERp, nER, Wfull, j, erv, nER);
+      scale_cols<T>(s, erv, nER, keep, nER, sgn);
+      double nrm = host_norm(erv, nER * keep);
+      FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "right environment vanished");
+      scale_by_inv<T>(s, erv, nER * keep, e->d_scal);
+      rs_M = rs;
+      rs += std::log(nrm);
+      Arena ernew = arena();
+      Env3 ERn = env_from_vectors(ernew, erv, keep, sl.bR, sl.tp);
+      e->spectra.fit[c - 1] = skeep;
+      qright = qk;
+      qout[c] = qk;
+      FP_CUDA(cudaStreamSynchronize(s));
+      ermem.reset();
+      ermem.live = ernew.live;
+      ernew.live.clear();
+      ER = ERn;
+      mmem.reset();
+      mmem.live = mnew.live;
+      mnew.live.clear();
+      M = Mnext;
+      a_c = keep;
+      a_prev = a2;
+    }
     const int Dn0 = bund(e->sites[e->layer][row * Ly], 3);
     const int64_t n0 = (int64_t)Dn0 * a_c;
     double nrm = host_norm(M, n0);

@@ -944,6 +944,23 @@ void scatter_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx,
   FP_LAUNCH();
 }
 
+// dst (cols x rows, column-major, ld ldd) = transpose of src (rows x cols, ld lds)
+template <class T>
+__global__ void k_transpose_block(const T* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+                                  T* __restrict__ dst, int64_t ldd) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / rows, i = e % rows;
+    dst[i * ldd + j] = src[j * lds + i];
+  }
+}
+template <class T>
+void transpose_block(cudaStream_t s, const T* src, int64_t lds, int64_t rows, int64_t cols, T* dst, int64_t ldd) {
+  if (rows * cols == 0) return;
+  k_transpose_block<T><<<grid_for(rows * cols), 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
+  FP_LAUNCH();
+}
+
 #define INST(T)                                                                                              \
   template void gaussian_sketch<T>(cudaStream_t, T*, int64_t, int64_t, int64_t, const int64_t*, uint64_t,    \
                                    uint64_t, uint64_t, uint64_t);                                            \
@@ -963,7 +980,8 @@ void scatter_rows(cudaStream_t s, const T* src, int64_t lds, const int64_t* idx,
   template void set_identity<T>(cudaStream_t, T*, int64_t, int);                                              \
   template void copy_cols<T>(cudaStream_t, const T*, int64_t, int, T*);                                      \
   template void gather_rows<T>(cudaStream_t, const T*, int64_t, const int64_t*, int64_t, int64_t, T*, int64_t);   \
-  template void scatter_rows<T>(cudaStream_t, const T*, int64_t, const int64_t*, int64_t, int64_t, T*, int64_t);
+  template void scatter_rows<T>(cudaStream_t, const T*, int64_t, const int64_t*, int64_t, int64_t, T*, int64_t); \
+  template void transpose_block<T>(cudaStream_t, const T*, int64_t, int64_t, int64_t, T*, int64_t);
 INST(float)
 INST(double)
 template void fill<int>(cudaStream_t, int*, int64_t, int);

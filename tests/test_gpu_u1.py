@@ -75,14 +75,20 @@ def test_u1_zipup_tf32x3(fp):
     assert abs(lg - ln_o) < 1e-4
 
 
-def test_u1_fit_is_not_built(fp):
-    peps, qpeps, W, qW, _, _ = _case(1)
-    env = fp.Env(peps, W, D=2, p=4, w=6, chi=6, prec="f64", seed=5, charges=fp.pack_charges(qpeps, qW))
+@pytest.mark.parametrize("chi", [4, 12])
+def test_u1_cbe_fit_matches_symmetric_oracle(fp, chi):
+    """Zip-up plus the sector-wise CBE fit (Fig. 3-5), same sketches on both sides."""
+    peps, qpeps, W, qW, Wl, qWl = _case(1)
+    prm = B.RsvdParams(oversample=4, power_iters=2, n_fit=1, chi_tilde=2)
+    sn_o, ln_o = S.contract_u1(peps, qpeps, Wl, qWl, chi, prm, seed=5, layer=1)
+    env = fp.Env(peps, W, D=2, p=4, w=6, chi=chi, prec="f64", seed=5, charges=fp.pack_charges(qpeps, qW))
     try:
-        fp.fpeps_absorb_row(env.h, 0, 1)
-        fp.fpeps_absorb_row(env.h, 1, 1)
-        with pytest.raises(fp.FpepsError) as e:
-            fp.fpeps_compress_rsvd(env.h, fp.params(4, 2, 0, 1, 0))
-        assert e.value.status == 7          # FPEPS_ERR_UNSUPPORTED
+        for r in range(3):
+            fp.fpeps_absorb_row(env.h, r, 1)
+            if r == 1:
+                fp.fpeps_compress_rsvd(env.h, fp.params(4, 2, 2, 1, 0))
+        sg, lg = fp.fpeps_sweep_value(env.h)
     finally:
         env.close()
+    assert sg == sn_o
+    assert abs(lg - ln_o) < 1e-9
