@@ -92,3 +92,20 @@ def test_u1_cbe_fit_matches_symmetric_oracle(fp, chi):
         env.close()
     assert sg == sn_o
     assert abs(lg - ln_o) < 1e-9
+
+
+def test_u1_expect_public_api(fp):
+    """<H> through fpeps_expect (operator and norm sweeps, zip-up + CBE fit) in the
+    charge-sector mode; at chi = 12 every cut of both layers lies between distinct
+    values or at the full rank."""
+    peps, qpeps, W, qW, _, _ = _case(1)
+    prm = B.RsvdParams(oversample=4, power_iters=2, n_fit=1, chi_tilde=2)
+    e_o, (sn_o, ln_o), (sd_o, ld_o) = S.expectation_u1(peps, qpeps, W, qW, 12, prm, seed=5)
+    env = fp.Env(peps, W, D=2, p=4, w=6, chi=12, prec="f64", seed=5, charges=fp.pack_charges(qpeps, qW))
+    try:
+        val, sn, ln = env.expect(fp.params(4, 2, 2, 1, 0))
+    finally:
+        env.close()
+    assert sn == sn_o                       # sign and ln|.| of <psi|H|psi>
+    assert abs(ln - ln_o) < 1e-9
+    assert abs(val - e_o) <= 1e-9 * abs(e_o)
