@@ -696,39 +696,26 @@ struct Engine : EngineBase {
         FP_CHECK((int64_t)QD.size() == 2 * st.bD && (int64_t)QR.size() == 2 * st.bR &&
                      (int64_t)qt.size() == 2 * st.tp && (int64_t)qa.size() == 2 * a,
                  FPEPS_ERR_STATE, "charge sectors: charge lists do not match the bonds");
-        using Key = std::pair<int32_t, int32_t>;
-        std::map<Key, std::vector<int64_t>> rmap, cmap;
+        std::vector<int32_t> rowq(2 * rows), colq(2 * cols);
         for (int64_t d = 0; d < st.bD; ++d)
           for (int64_t ai = 0; ai < a; ++ai)
-            rmap[{qa[2 * ai] - QD[2 * d], qa[2 * ai + 1] - QD[2 * d + 1]}].push_back(d * a + ai);
+            for (int t = 0; t < 2; ++t) rowq[2 * (d * a + ai) + t] = qa[2 * ai + t] - QD[2 * d + t];
         for (int64_t R = 0; R < st.bR; ++R)
           for (int64_t tq = 0; tq < st.tp; ++tq)
-            cmap[{qt[2 * tq] + QR[2 * R], qt[2 * tq + 1] + QR[2 * R + 1]}].push_back(R * st.tp + tq);
-        struct Sec {
-          Key q;
-          std::vector<int64_t> ri, ci;
-          int64_t *d_ri = nullptr, *d_ci = nullptr;
-          int cap = 0, k = 0;
-          T *L = nullptr, *Rv = nullptr;
-          std::vector<double> sig;
-        };
-        std::vector<Sec> secs;
-        for (auto& kv : rmap) {
-          auto it = cmap.find(kv.first);
-          if (it == cmap.end()) continue;
-          Sec x;
-          x.q = kv.first;
-          x.ri = kv.second;
-          x.ci = it->second;
-          const int64_t rank = std::min<int64_t>((int64_t)x.ri.size(), (int64_t)x.ci.size());
-          x.cap = (int)std::min<int64_t>(chi, rank);
-          if (x.cap == 0) continue;
-          x.k = prm.exact_svd ? (int)rank : (int)std::min<int64_t>((int64_t)x.cap + prm.oversample, rank);
-          secs.push_back(std::move(x));
-        }
-        FP_CHECK(!secs.empty(), FPEPS_ERR_NUMERIC, "charge sectors: rows and columns share no charge");
+            for (int t = 0; t < 2; ++t) colq[2 * (R * st.tp + tq) + t] = qt[2 * tq + t] + QR[2 * R + t];
+        std::vector<SecIdx> secs = sectors_of(ar, rowq, colq);
+        const size_t ns = secs.size();
+        std::vector<int> cap(ns), kq(ns);
         int kmax = 0;
-        for (auto& x : secs) kmax = std::max(kmax, x.k);
+        int64_t capsum = 0;
+        for (size_t n = 0; n < ns; ++n) {
+          const int64_t rank = std::min<int64_t>((int64_t)secs[n].ri.size(), (int64_t)secs[n].ci.size());
+          cap[n] = (int)std::min<int64_t>(chi, rank);
+          kq[n] = prm.exact_svd ? (int)rank : (int)std::min<int64_t>((int64_t)cap[n] + prm.oversample, rank);
+          kmax = std::max(kmax, kq[n]);
+          capsum += cap[n];
+        }
+        FP_CHECK(capsum > 0, FPEPS_ERR_NUMERIC, "charge sectors: rows and columns share no charge");
         T* omega = ar.get_n<T>(cols * kmax);
         int64_t perm[2] = {st.bR, st.tp};
         gaussian_sketch<T>(s, omega, cols, kmax, cols, perm, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c, w3);
@@ -736,16 +723,15 @@ struct Engine : EngineBase {
         T* fullr = ar.get_n<T>(rows * kmax);
         Env3 elc = EL[c];
         double tot = 0.0;
-        for (auto& x : secs) {
-          const int64_t nr = (int64_t)x.ri.size(), nc = (int64_t)x.ci.size();
-          x.d_ri = ar.get_n<int64_t>(nr);
-          x.d_ci = ar.get_n<int64_t>(nc);
-          FP_CUDA(cudaMemcpyAsync(x.d_ri, x.ri.data(), sizeof(int64_t) * nr, cudaMemcpyHostToDevice, s));
-          FP_CUDA(cudaMemcpyAsync(x.d_ci, x.ci.data(), sizeof(int64_t) * nc, cudaMemcpyHostToDevice, s));
-          T* om = ar.get_n<T>(nc * x.k);
-          gather_rows<T>(s, omega, cols, x.d_ci, nc, x.k, om, nc);
-          const int64_t* dri = x.d_ri;
-          const int64_t* dci = x.d_ci;
+        std::vector<T*> Ls(ns, nullptr), Rs(ns, nullptr);
+        std::vector<std::vector<double>> sig(ns);
+        std::vector<Pick> cand;
+        for (size_t n = 0; n < ns; ++n) {
+          const int64_t nr = (int64_t)secs[n].ri.size(), nc = (int64_t)secs[n].ci.size();
+          const int64_t* dri = secs[n].d_ri;
+          const int64_t* dci = secs[n].d_ci;
+          T* om = ar.get_n<T>(nc * kq[n]);
+          gather_rows<T>(s, omega, cols, dci, nc, kq[n], om, nc);
           Lin A{nr, nc,
                 [&, dri, dci, nr, nc](const T* X, T* Y, int64_t kk) {
                   FP_CUDA(cudaMemsetAsync(fullc, 0, sizeof(T) * cols * kk, s));
@@ -759,36 +745,20 @@ struct Engine : EngineBase {
                   theta_t(st, elc, fullr, fullc, kk);
                   gather_rows<T>(s, fullc, cols, dci, nc, kk, Z, nc);
                 }};
-          RsvdOut r = rsvd(ar, A, om, x.k, prm.power_iters);
-          T* Ut = ar.get_n<T>((int64_t)x.k * x.k);
-          convert_f64<T>(s, r.U, Ut, (int64_t)x.k * x.k);
-          x.L = ar.get_n<T>(nr * x.k);
-          mm_right(nr, x.k, x.k, r.Q, nr, Ut, x.k, x.L, nr);
-          x.Rv = r.QbW;
-          x.sig = r.sigma;
+          RsvdOut r = rsvd(ar, A, om, kq[n], prm.power_iters);
+          T* Ut = ar.get_n<T>((int64_t)kq[n] * kq[n]);
+          convert_f64<T>(s, r.U, Ut, (int64_t)kq[n] * kq[n]);
+          Ls[n] = ar.get_n<T>(nr * kq[n]);
+          mm_right(nr, kq[n], kq[n], r.Q, nr, Ut, kq[n], Ls[n], nr);
+          Rs[n] = r.QbW;
+          sig[n] = r.sigma;
           for (double v : r.sigma) tot += v * v;
+          for (int j = 0; j < cap[n]; ++j) cand.push_back({-r.sigma[j], (int)n, j});
         }
         // global truncation: the chi_c largest over the sectors' offers (ties: sector
         // order, then index); kept triplets ordered by sector, then value
-        struct Cand {
-          double v;
-          int n, j;
-        };
-        std::vector<Cand> cand;
-        int64_t capsum = 0;
-        for (int n = 0; n < (int)secs.size(); ++n) {
-          capsum += secs[n].cap;
-          for (int j = 0; j < secs[n].cap; ++j) cand.push_back({-secs[n].sig[j], n, j});
-        }
         const int chi_c = (int)std::min<int64_t>(chi, capsum);
-        auto lex = [](const Cand& x, const Cand& y) {
-          return x.v != y.v ? x.v < y.v : (x.n != y.n ? x.n < y.n : x.j < y.j);
-        };
-        std::sort(cand.begin(), cand.end(), lex);
-        cand.resize(chi_c);
-        std::sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) {
-          return x.n != y.n ? x.n < y.n : x.j < y.j;
-        });
+        std::vector<Pick> kept = pick_global(cand, chi_c);
         T* N = rowmem.get_n<T>(rows * chi_c);
         T* elv = rowmem.get_n<T>(cols * chi_c);
         FP_CUDA(cudaMemsetAsync(N, 0, sizeof(T) * rows * chi_c, s));
@@ -797,12 +767,12 @@ struct Engine : EngineBase {
         std::vector<int32_t> qk(2 * (size_t)chi_c);
         double kept2 = 0.0;
         for (int m = 0; m < chi_c; ++m) {
-          const Sec& x = secs[cand[m].n];
-          const int j = cand[m].j;
+          const int n = kept[m].n, j = kept[m].j;
+          const SecIdx& x = secs[n];
           const int64_t nr = (int64_t)x.ri.size(), nc = (int64_t)x.ci.size();
-          scatter_rows<T>(s, x.L + (int64_t)j * nr, nr, x.d_ri, nr, 1, N + (int64_t)m * rows, rows);
-          scatter_rows<T>(s, x.Rv + (int64_t)j * nc, nc, x.d_ci, nc, 1, elv + (int64_t)m * cols, cols);
-          sv[m] = x.sig[j];
+          scatter_rows<T>(s, Ls[n] + (int64_t)j * nr, nr, x.d_ri, nr, 1, N + (int64_t)m * rows, rows);
+          scatter_rows<T>(s, Rs[n] + (int64_t)j * nc, nc, x.d_ci, nc, 1, elv + (int64_t)m * cols, cols);
+          sv[m] = sig[n][j];
           kept2 += sv[m] * sv[m];
           alive[m] = (tot > 0 && sv[m] * sv[m] > 1e-30 * tot) ? 1.0 : 0.0;
           qk[2 * m] = x.q.first;
