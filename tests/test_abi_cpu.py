@@ -77,3 +77,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(fpeps, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(fpeps.FpepsError):
         fpeps.lib()
+
+
+def test_pack_charges_layout():
+    """Charge marshalling follows the header: PEPS sites (legs l,u,r,d, dim pairs each),
+    then PEPO sites, row-major, int32."""
+    import numpy as np
+    from paper_2511_01039_gb300 import fpeps
+    from synth import lattice as L
+    from synth import u1
+    Lx, Ly, D = 3, 4, 2
+    peps, ch = u1.u1_peps(Lx, Ly, D, 1)
+    qpeps = [[u1.peps_leg_charges(ch, Lx, Ly, r, c) for c in range(Ly)] for r in range(Lx)]
+    ham = L.hubbard_hamiltonian(Lx, Ly, 1)
+    W, qW = L.fsm_pepo(ham), u1.hubbard_pepo_charges(ham)
+    q = fpeps.pack_charges(qpeps, qW)
+    assert q.dtype == np.int32
+    n_a = sum(2 * sum(peps[r][c].shape[:4]) for r in range(Lx) for c in range(Ly))
+    n_w = sum(2 * sum(W[r][c].shape[:4]) for r in range(Lx) for c in range(Ly))
+    assert q.size == n_a + n_w
+    # first site: legs l, u, r, d in order, each (dim, 2) flattened
+    ql, qu, qr, qd = qpeps[0][0]
+    head = np.concatenate([ql.reshape(-1), qu.reshape(-1), qr.reshape(-1), qd.reshape(-1)])
+    assert np.array_equal(q[:head.size], head)
+    assert fpeps.pack_charges(qpeps).size == n_a
