@@ -157,6 +157,52 @@ def cpu_sample(seconds: float, workload):
 
 
 # ----------------------------------------------------------------------------- ranks
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of a
+# kernel class, from one ncu capture of the probe case (bench.py --probe-theta 8: both
+# GEMM launches, one sandwich launch); traffic per launch = ratio x the algorithmic
+# bytes of an average launch (traffic grows with the bytes moved)
+DRAM_PER_ALG_BYTE = {"gemm_tc_tf32x3": (0.911 + 1.020) / (2 * 0.966), "sandwich": 1.837 / 1.493}
+
+
+def roofline_of(kind: str, d: dict, prec: str, peaks: dict) -> dict:
+    """Roofline of one kernel class from its profile record (launches, ms, algorithmic
+    flops and bytes). The bound is the resource that caps the class at its own
+    arithmetic intensity: for a tensor-core class in 3xTF32 the compute ceiling is the
+    TF32 peak / 3 (three MMAs per algorithmic product), and below the ridge point
+    (ceiling / HBM bandwidth) the class is HBM-bound and is reported in GB/s."""
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "of measured" if peaks else "of fallback"
+    ms = d["ms"]
+    tflops = d["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    gbs = d["bytes"] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    traffic = None
+    if kind in DRAM_PER_ALG_BYTE and d["launches"]:
+        traffic = DRAM_PER_ALG_BYTE[kind] * d["bytes"] / d["launches"]
+    intensity = d["flops"] / d["bytes"] if d["bytes"] > 0 else float("inf")   # flop per byte
+    tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if prec == "tf32x3" else ("gemm_tc_tf32x3",)
+    if kind in tensor_kinds:
+        peak = bf16 * 1.1 / 2.25               # TF32 dense peak = BF16 x nominal TF32/BF16 ratio
+        ridge = (peak / 3.0) * 1e12 / (hbm * 1e9)
+        if intensity >= ridge:
+            return {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                    "traffic": traffic, "kernel": kind,
+                    "note": f"TF32 peak = {src} BF16 x 1.1/2.25; algorithmic flops, and 3xTF32 issues 3 MMAs per "
+                            f"product, so frac <= 1/3"}
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
+                "kernel": kind,
+                "note": f"{intensity:.1f} algorithmic flop/byte, below the 3xTF32 ridge of {ridge:.1f} flop/byte "
+                        f"(TF32 peak / 3 over the HBM bandwidth, both {src}): HBM-bound, algorithmic bytes; "
+                        f"{tflops:.1f} TFLOP/s"}
+    if kind in ("gemm_simt", "sandwich"):
+        peak = 80.0
+        return {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                "traffic": None, "kernel": kind,
+                "note": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz ~ 80 TFLOP/s"}
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+            "kernel": kind}
+
+
 def reduce_ranks(dist, dev, seconds, work):
     """Replicas exchange nothing on the data path; the timing is the slowest rank's
     and the work is the sum over ranks. Returns (max seconds, summed work)."""
@@ -342,37 +388,7 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    bf16 = peaks.get("bf16_tflops", 1900.0)
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    src = "of measured" if peaks else "of fallback"
-    d = prof[dom]
-    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of
-    # the kernel, from one ncu capture of the probe case (bench.py --probe-theta 8:
-    # both GEMM launches, one sandwich launch); traffic per launch = ratio x the
-    # algorithmic bytes of an average launch here (traffic grows with the bytes moved)
-    dram_per_alg_byte = {"gemm_tc_tf32x3": (0.911 + 1.020) / (2 * 0.966), "sandwich": 1.837 / 1.493}
-    traffic = None
-    if dom in dram_per_alg_byte and d["launches"]:
-        traffic = dram_per_alg_byte[dom] * d["bytes"] / d["launches"]
-    tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if args.prec == "tf32x3" else ("gemm_tc_tf32x3",)
-    if dom in tensor_kinds:
-        # TF32 dense peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1/2.25)
-        peak = bf16 * 1.1 / 2.25
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
-                "note": f"TF32 peak = {src} BF16 x 1.1/2.25; algorithmic flops, and 3xTF32 issues 3 MMAs per "
-                        f"product, so frac <= 1/3"}
-    elif dom in ("gemm_simt", "sandwich"):
-        peak = 80.0
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom,
-                "note": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz ~ 80 TFLOP/s"}
-    else:
-        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": dom}
+    roof = roofline_of(dom, prof[dom], args.prec, peaks)
     # achieved TFLOP/s and GB/s (algorithmic flops and bytes / device time) per kernel class;
     # the sketch and the Gram pass of the QR stream their operand through HBM once
     per_kind = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
