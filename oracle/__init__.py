@@ -16,8 +16,9 @@ It restates, slowly and in double precision, what the GPU path computes:
                  CBE variational fit whose A*Omega follows Fig. 5.
 * ``symmetric`` - the U(1) x U(1) block-sparse mode (Sec. III quantum-number
                  slicing, Sec. V symmetric Hubbard runs): the zip-up with a
-                 sector-wise rSVD and one global truncation, on the dense
-                 applications of ``boundary``.
+                 sector-wise rSVD and one global truncation, and the CBE fit
+                 with a sector-wise CBE rSVD and a sector-wise SVD of the
+                 fitted tensor, on the dense applications of ``boundary``.
 
 It shares no code with the CUDA path; the only common module is the seeded
 input generator ``synth`` (data, no method arithmetic).

@@ -24,9 +24,11 @@ Bundles (L, U, R, Dn) are flattened (ket, PEPO, bra) legs, bra fastest.
 Readings where the paper is silent (each is listed with its reason in the
 design notes): kept bond chi_c = min(chi, rows, cols) of the matrix factorised;
 sketch width chi_c + oversampling; q power iterations with re-orthonormalisation
-after every application; CBE width ceil(chi/10); singular-vector signs fixed so
-that every kept vector has a non-negative entry sum; per-site Frobenius
-normalisation with the logarithms accumulated.
+after every application; CBE width ceil(chi/10), clipped to the dimensions of
+the complement; singular-vector signs fixed so that every kept vector x has
+sum_i w_i x_i >= 0 for fixed Gaussian weights w drawn by the sketch generator
+(``gauge_signs``); per-site Frobenius normalisation with the logarithms
+accumulated.
 """
 from __future__ import annotations
 
@@ -248,8 +250,38 @@ def zipup(T, Arow, Wrow, chi: int, prm: RsvdParams, *, seed: int, layer: int, ro
     return N, ELs, log_s, spectra
 
 
+def cbe_operator(two_site, two_site_t, V, Nlm):
+    """The CBE matrix A = P_L^perp Theta2s P_R^perp and its transpose as maps (Fig. 5).
+
+    V (rows orthonormal) spans the row space of the centre tensor, so
+    P_R^perp = I - V^T V; Nlm (columns orthonormal) is the left isometry of the
+    zip-up at the left site, so P_L^perp = I - Nlm Nlm^T. Neither projector is
+    formed: the right one is split into the identity minus the tangent
+    projector and the two clusters Theta2s(X) and Theta2s(V^T V X) are
+    contracted separately and subtracted (Fig. 5(b)-(e)); the left one is then
+    applied to the result (Fig. 5(f)-(g)). The transpose runs the mirror image.
+    """
+
+    def a_apply(X):
+        y = two_site(X) - two_site(V.T @ (V @ X))
+        return y - Nlm @ (Nlm.T @ y)
+
+    def a_apply_t(Y):
+        z = two_site_t(Y) - two_site_t(Nlm @ (Nlm.T @ Y))
+        return z - V.T @ (V @ z)
+
+    return a_apply, a_apply_t
+
+
+def cbe_width(chi_t: int, rows_a: int, n_left: int, cols_a: int, n_right: int) -> int:
+    """Number of expansion vectors: chi_tilde, clipped to the dimensions of the
+    complement (rows outside the left isometry's n_left columns, columns outside
+    the n_right rows of V), which bound the rank of A."""
+    return min(chi_t, rows_a - n_left, cols_a - n_right)
+
+
 def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, layer: int, row: int,
-            env: int = 0):
+            env: int = 0, trace: list | None = None):
     """Right-to-left variational fit with controlled bond expansion (Fig. 3-5).
 
     At each bond (c-1, c): V = row basis of the centre tensor at c; the
@@ -257,6 +289,9 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
     P_R^perp, by rSVD) widens V to V' = [V; Vtil]; the expanded right
     environment and the fitted tensor M' at c-1 follow pattern 2(a); the SVD of
     M' truncates the bond back. Returns (new T, log_scale, spectra).
+
+    ``trace`` (test hook, no effect on the result): if a list is given, one dict
+    per bond is appended with the inputs and outputs of the expansion step.
     """
     Ly = len(T)
     chi_t = prm.chi_tilde if prm.chi_tilde > 0 else -(-chi // 10)
@@ -279,7 +314,7 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
         Nl = N[c - 1]
         Nlm = Nl.reshape(-1, Nl.shape[2])                           # (a_{c-2} Dn_{c-1}) x a_{c-1}
         rows_a, cols_a = Nlm.shape[0], dDn * a_c
-        ct = min(chi_t, rows_a - Nlm.shape[1], cols_a - a_eff)
+        ct = cbe_width(chi_t, rows_a, Nlm.shape[1], cols_a, a_eff)
         ELl = ELs[c - 1]
         a2, dDnl = ELl.shape[0], bdim(Al, Wl, 3)
 
@@ -291,25 +326,18 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
             z = theta_t(ELl, T[c - 1], Al, Wl, Y.reshape(a2, dDnl, -1))
             return theta_r_t(ER, T[c], A, W, z).reshape(cols_a, -1)
 
-        def a_apply(X):
-            # Fig. 5(b)-(e): P_R^perp X = X - V^T V X, applied as two clusters and subtracted
-            y = two_site(X) - two_site(V.T @ (V @ X))
-            # Fig. 5(f)-(g): the left projector likewise
-            return y - Nlm @ (Nlm.T @ y)
+        a_apply, a_apply_t = cbe_operator(two_site, two_site_t, V, Nlm)
 
-        def a_apply_t(Y):
-            z = two_site_t(Y) - two_site_t(Nlm @ (Nlm.T @ Y))
-            return z - V.T @ (V @ z)
-
+        sa, vtil, k = np.zeros(0), np.zeros((0, cols_a)), 0
         if ct > 0:
             k = min(ct + prm.oversample, rows_a, cols_a)
             omega = gaussian_sketch(cols_a, k, seed=seed, layer=layer, stage=1, site=c, row=row, env=env)
             _, _, sa, vt = rsvd(a_apply, a_apply_t, omega, prm.power_iters)
-            vt = vt * live(sa)[:, None]
+            vtil = (vt * live(sa)[:, None])[:ct]
             # the kept singular vectors lie in range(P_R^perp) unless A is (numerically)
             # rank deficient, when null-space vectors are arbitrary: a thin QR of
             # [V^T, Vtil^T] keeps V and makes the added rows orthogonal to it
-            Vp = orth(np.hstack([V.T, vt[:ct].T])).T
+            Vp = orth(np.hstack([V.T, vtil.T])).T
         else:
             Vp = V
         ERp = theta_r(ER, T[c], A, W, Vp.T.reshape(dDn, a_c, -1))   # [t_{c-1}, L_c, j]
@@ -323,6 +351,9 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
         out[c] = nc.reshape(keep, dDn, a_c)
         M = ((u[:, :keep] * s[:keep]) * sg[None, :]).reshape(a2, dDnl, keep)
         er = (sg[:, None] * wt[:keep]) @ ERp.reshape(-1, ERp.shape[2]).T    # keep x (t L)
+        if trace is not None:
+            trace.append(dict(c=c, V=V, Nlm=Nlm, ct=ct, k=k, sigma_a=sa, Vtil=vtil, Vp=Vp, ER=ER, EL=ELl,
+                              rows_a=rows_a, cols_a=cols_a, spectrum=s[:keep].copy()))
         nrm = np.linalg.norm(er)
         rs_M = rs
         rs += math.log(nrm)
