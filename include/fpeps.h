@@ -144,27 +144,61 @@ fpeps_status fpeps_absorb_row(fpeps_env* env, int32_t row, int32_t layer);
  * factorisation broke down or a value became non-finite. */
 fpeps_status fpeps_compress_rsvd(fpeps_env* env, const fpeps_rsvd_params* params, fpeps_stats* out_host);
 
-/* Value of the sweep closed by the last absorbed row: sign and ln|value|. */
+/* Value of the network closed by the last absorbed row (Sec. II: the energy
+ * functional <psi|O|psi>, or <psi|psi> for layer 0, as the sandwich of PEPS,
+ * PEPO and adjoint PEPS contracted through the boundary MPS).
+ *   log_abs, sign  host pointers; value = sign * exp(log_abs) (the log form keeps
+ *                  lattices whose value under- or overflows a double).
+ * Errors: FPEPS_ERR_ARG (NULL pointers), FPEPS_ERR_STATE (no sweep has been
+ * closed since the last row 0). Reads host state only; no GPU work. */
 fpeps_status fpeps_sweep_value(fpeps_env* env, double* log_abs, int32_t* sign);
 
-/* Full sweep with the identity PEPO: <psi|psi> = sign * exp(log_abs). */
+/* <psi|psi> of the PEPS (Sec. II: the norm network, PEPS and adjoint PEPS with
+ * the identity in place of the PEPO, w = 1), by one top-to-bottom boundary sweep
+ * of layer 0: row 0 exactly, every interior row compressed by fpeps_compress_rsvd
+ * with `params` (Sec. IV), the last row closed exactly.
+ *   params         rSVD / CBE settings (read during the call).
+ *   log_abs, sign  host pointers: <psi|psi> = sign * exp(log_abs).
+ * Any row state of the env is replaced (a new sweep starts at row 0). Synchronises
+ * the env stream. Errors: FPEPS_ERR_ARG (NULL pointers), FPEPS_ERR_NUMERIC
+ * (non-finite input or a factorisation breakdown), FPEPS_ERR_OOM, FPEPS_ERR_CUDA,
+ * FPEPS_ERR_TIMEOUT (a bounded device wait gave up). */
 fpeps_status fpeps_contract_norm(fpeps_env* env, const fpeps_rsvd_params* params, double* log_abs,
                                  int32_t* sign);
 
-/* Full sweeps with the operator PEPO (layer 1) and the identity (layer 0):
- * value = <psi|O|psi> / <psi|psi>; the numerator as (sign_num, log_abs_num).
- * Errors: FPEPS_ERR_STATE if the env has no operator PEPO. */
+/* Expectation value <O> = <psi|O|psi> / <psi|psi> (Sec. II: the energy
+ * functional E = <psi|H|psi> of Fig. 1, normalised by the norm network): one
+ * boundary sweep with the operator PEPO (layer 1) and one with the identity
+ * (layer 0), each as in fpeps_contract_norm, with the same sketch seed.
+ *   params       rSVD / CBE settings (read during the call).
+ *   value        host pointer: <O>.
+ *   log_abs_num, sign_num  host pointers: <psi|O|psi> = sign_num * exp(log_abs_num).
+ * Synchronises the env stream. Errors: FPEPS_ERR_STATE if the env has no operator
+ * PEPO; otherwise as fpeps_contract_norm. */
 fpeps_status fpeps_expect(fpeps_env* env, const fpeps_rsvd_params* params, double* value,
                           double* log_abs_num, int32_t* sign_num);
 
-/* Checkpoint of the current boundary (after row 0 or a compressed row).
+/* Checkpoint of the current boundary (after row 0 or a compressed row). The
+ * paper has no counterpart: this is the library's restart format (the boundary
+ * MPS of Sec. II after the rows absorbed so far, with its accumulated scale).
  * Layout: int64 header {magic, Ly, next_row, layer, elem_bytes, bond[Ly+1],
  * phys[Ly]}, double log_scale, then the tensors T_c in compute precision.
- * With host_buf == NULL, *bytes receives the required size. */
+ *   host_buf  host memory of *bytes bytes, or NULL: then *bytes receives the
+ *             required size and nothing is copied.
+ * A staged row that has not been compressed yet is not part of the checkpoint.
+ * Synchronises the env stream. Errors: FPEPS_ERR_ARG (NULL bytes, or a buffer
+ * smaller than the checkpoint), FPEPS_ERR_STATE (no boundary yet, or the sweep
+ * has been closed by its last row), FPEPS_ERR_CUDA. */
 fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes);
 
 /* Load a boundary (same layout as fpeps_export_boundary, from any source with
- * the right shapes) and make `next_row` the next row to absorb in `layer`.
+ * the right shapes) and make `next_row` the next row to absorb in `layer`. The
+ * paper has no counterpart: this restarts a sweep from a stored boundary MPS
+ * (Sec. II). Errors: FPEPS_ERR_ARG (bad magic, element size, lattice width, end
+ * bonds or byte count; next_row outside 1..Lx-1), FPEPS_ERR_STATE (layer 1 without
+ * an operator PEPO), FPEPS_ERR_OOM, FPEPS_ERR_CUDA. Bundles that do not match the
+ * up legs of row `next_row` are reported by the next fpeps_compress_rsvd or
+ * closing fpeps_absorb_row (FPEPS_ERR_ARG).
  * `host_buf` may point to host memory (copied host -> device, the call
  * synchronises) or to device memory (copied device -> device on the env
  * stream, only the header is read back). The buffer must stay valid until the

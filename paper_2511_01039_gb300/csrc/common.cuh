@@ -169,6 +169,10 @@ template <class T>
 void frob_norm_f64(cudaStream_t s, const T* x, int64_t n, double* out);
 template <class T>
 void scale_by_inv(cudaStream_t s, T* x, int64_t n, const double* nrm);
+// out[0] = <x, r> / <r, r> in FP64 (1 if that is not a positive finite number);
+// out: >= 2 doubles of device memory
+template <class T>
+void scale_against(cudaStream_t s, const T* x, const T* r, int64_t n, double* out);
 
 template <class T>
 void permute3(cudaStream_t s, const T* in, T* out, int64_t d0, int64_t d1, int64_t d2, int p0, int p1, int p2);
@@ -178,6 +182,13 @@ void transpose_pad(cudaStream_t s, const T* src, int64_t rows, int64_t cols, int
 // out = a - b elementwise (out may alias a or b)
 template <class T>
 void sub_into(cudaStream_t s, T* out, const T* a, const T* b, int64_t n);
+// out(i, j) += X(i, j) * R[j * k + j] for i < m, j < n (X, out column-major; R row-major FP64 k x k)
+template <class T>
+void add_diag_cols(cudaStream_t s, const T* X, int64_t m, int n, int64_t ldx, const double* R, int k, T* out,
+                   int64_t ldo);
+// A[j * ld + j] = 0 for j < k
+template <class T>
+void zero_diag(cudaStream_t s, T* A, int k, int64_t ld);
 // dst (col-major rows x cols) = (T) src (row-major rows x cols)
 template <class T>
 void convert_f64_t(cudaStream_t s, const double* src, int64_t rows, int64_t cols, T* dst);

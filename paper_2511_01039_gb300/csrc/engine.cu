@@ -132,6 +132,9 @@ struct Engine : EngineBase {
   double flops = 0.0;
   double trunc_num = 0.0, trunc_den = 0.0;
   size_t budget_elems = (size_t)1 << 30;   // per-chunk intermediate size (elements)
+  // true while an application runs entirely on the CUDA cores (FP32, round to
+  // nearest): the reference columns of a scale calibration (see apply())
+  bool simt_only = false;
   void* scr[2] = {nullptr, nullptr};
   size_t scr_n[2] = {0, 0};
   void* tc_scr = nullptr;
@@ -187,7 +190,8 @@ struct Engine : EngineBase {
     if (count) flops += 2.0 * (double)M * (double)N * (double)K;
     // tensor cores for every contraction with at least one full 128x128x32 tile and
     // 16-byte aligned rows; smaller edge contractions stay on the CUDA cores (FP32)
-    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && gemm_tc_supported(M, N, K, lda, ldb) &&
+    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && !simt_only &&
+        gemm_tc_supported(M, N, K, lda, ldb) &&
         ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0) {
       size_t need = gemm_tc_scratch_bytes(mode, M, N, K);
       if (!tc_scr || tc_n < need) {
@@ -216,9 +220,19 @@ struct Engine : EngineBase {
   // out (m x n, col-major, ld ldo) = X (m x k, col-major, ld ldx) S (k x n, col-major, ld lds): a tall
   // matrix times a small one. In 3xTF32 mode with at least one full tile this runs on the tensor
   // cores through K-major copies (X transposed, S with its rows padded to a multiple of 4).
-  void mm_right(int64_t m, int n, int k, const T* X, int64_t ldx, const T* S, int64_t lds, T* out, int64_t ldo) {
+  // The truncating FP32 accumulation of the tensor cores scales every column of the result by
+  // 1 - beta_j, with beta_j set by the number of nonzero terms it sums (see apply()). Products
+  // whose scale reaches the contracted value are therefore made unbiased:
+  //   TALL_CALIBRATED  (S dense, so beta_j is the same for every column) the first two columns
+  //                    are recomputed on the CUDA cores and the result divided by the fitted factor;
+  //   TALL_CUDA_CORES  the whole product on the CUDA cores (FP32, round to nearest).
+  enum Tall { TALL_PLAIN = 0, TALL_CALIBRATED = 1, TALL_CUDA_CORES = 2 };
+  void mm_right(int64_t m, int n, int k, const T* X, int64_t ldx, const T* S, int64_t lds, T* out, int64_t ldo,
+                int how = TALL_PLAIN) {
     const int kp = (k + 3) & ~3;
-    if (sizeof(T) == 4 && mode == FPEPS_TF32X3 && gemm_tc_supported(m, n, k, kp, kp)) {
+    if (how == TALL_CALIBRATED && n <= kCalCols) how = TALL_CUDA_CORES;
+    if (sizeof(T) == 4 && mode == FPEPS_TF32X3 && how != TALL_CUDA_CORES && !simt_only &&
+        gemm_tc_supported(m, n, k, kp, kp)) {
       Arena ar = arena();
       T* Xt = ar.get_n<T>((size_t)m * kp);
       transpose_pad<T>(s, X, k, m, ldx, Xt, kp);
@@ -226,6 +240,18 @@ struct Engine : EngineBase {
       if (kp != k) FP_CUDA(cudaMemsetAsync(St, 0, sizeof(T) * n * kp, s));
       FP_CUDA(cudaMemcpy2DAsync(St, sizeof(T) * kp, S, sizeof(T) * lds, sizeof(T) * k, n, cudaMemcpyDeviceToDevice, s));
       big_gemm(m, n, k, Xt, kp, St, kp, out, out_colmajor(m, n, ldo), false);
+      if (how == TALL_CALIBRATED) {
+        T* ref = ar.get_n<T>((size_t)m * kCalCols);
+        mm(m, kCalCols, k, T(1), X, false, ldx, S, false, lds, T(0), ref, m);
+        double* alpha = env->d_scal + 6;
+        if (ldo == m) {
+          scale_against<T>(s, out, ref, m * kCalCols, alpha);
+          scale_by_inv<T>(s, out, m * n, alpha);
+        } else {   // strided output: fit on the first column, rescale column by column
+          scale_against<T>(s, out, ref, m, alpha);
+          for (int j = 0; j < n; ++j) scale_by_inv<T>(s, out + (int64_t)j * ldo, m, alpha);
+        }
+      }
       return;
     }
     mm(m, n, k, T(1), X, false, ldx, S, false, lds, T(0), out, ldo);
@@ -295,7 +321,7 @@ struct Engine : EngineBase {
   // modes when the site fits the tile, CUDA cores otherwise
   void sandwich(const SandOrient& o, int64_t nt, int64_t nk, const T* in, int64_t i_t, int64_t i_k, int64_t i_X,
                 int64_t i_Y, T* out, int64_t o_t, int64_t o_k, int64_t o_V, int64_t o_Z) {
-    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && sandwich_mma_fits(o)) {
+    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && !simt_only && sandwich_mma_fits(o)) {
       sandwich_apply_tc(s, o, nt, nk, (const float*)in, i_t, i_k, i_X, i_Y, (float*)out, o_t, o_k, o_V, o_Z);
       return;
     }
@@ -405,6 +431,68 @@ struct Engine : EngineBase {
     }
   }
 
+  // ---------------------------------------------------------------- calibrated applications
+  // The tensor cores add every MMA's products into the FP32 accumulator with
+  // truncation toward zero. Errors of that kind do not average out: each one
+  // shrinks the partial sum it rounds, so a tensor-core application returns the
+  // exact result times a common factor 1 - beta (measured on GB300: beta ~ 1.5e-6
+  // per 256-term accumulation chunk of the GEMM, 2e-6 to 6e-6 for a whole Theta_c
+  // application), and the contracted value, a product of one application per site
+  // and row, inherits the sum of those betas. Subspace iterations and the CBE
+  // expansion are insensitive to a common factor; the applications whose scale
+  // reaches the value (the fitted environments and tensors, the last zip-up
+  // application of a pass without fit, the closing row) are calibrated: the same
+  // application runs for the first kCalCols vectors on the CUDA cores (FP32 with
+  // round-to-nearest, unbiased), the least-squares factor
+  // alpha = <y_tc, y_ref> / <y_ref, y_ref> over those columns is formed on the
+  // device, and the whole output is divided by it. An application with at most
+  // kCalCols vectors runs on the CUDA cores outright.
+  static constexpr int kCalCols = 2;
+  enum Op { OP_THETA = 0, OP_THETA_T = 1, OP_THETA_R = 2, OP_THETA_R_T = 3 };
+  void run_op(int op, const Site& st, const Env3& e, const T* in, T* out, int64_t k) {
+    switch (op) {
+      case OP_THETA: theta(st, e, in, out, k); break;
+      case OP_THETA_T: theta_t(st, e, in, out, k); break;
+      case OP_THETA_R: theta_r(st, e, in, out, k); break;
+      default: theta_r_t(st, e, in, out, k); break;
+    }
+  }
+  int64_t op_out_size(int op, const Site& st, const Env3& e) const {
+    switch (op) {
+      case OP_THETA: return (int64_t)st.bD * e.a;
+      case OP_THETA_T: return (int64_t)st.bR * st.tp;
+      case OP_THETA_R: return (int64_t)st.bL * st.t;
+      default: return (int64_t)st.bD * e.a;
+    }
+  }
+  void apply(int op, const Site& st, const Env3& e, const T* in, T* out, int64_t k, bool calibrate) {
+    const bool tc = sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3);
+    if (!calibrate || !tc || simt_only) {
+      run_op(op, st, e, in, out, k);
+      return;
+    }
+    const double f0 = flops;
+    if (k <= kCalCols) {
+      simt_only = true;
+      run_op(op, st, e, in, out, k);
+      simt_only = false;
+      return;
+    }
+    run_op(op, st, e, in, out, k);
+    const int64_t nout = op_out_size(op, st, e);
+    Arena ar = arena();
+    T* ref = ar.get_n<T>((size_t)kCalCols * nout);
+    const double f1 = flops;
+    simt_only = true;
+    run_op(op, st, e, in, ref, kCalCols);   // inputs are [k][...]: the first kCalCols vectors
+    simt_only = false;
+    flops = f1;                              // the reference is not algorithmic work
+    double* alpha = env->d_scal + 4;
+    scale_against<T>(s, out, ref, (int64_t)kCalCols * nout, alpha);
+    scale_by_inv<T>(s, out, k * nout, alpha);
+    (void)f0;
+  }
+
   // ---------------------------------------------------------------- helpers
   Arena arena() { Arena ar; ar.al = &env->al; return ar; }
 
@@ -488,7 +576,13 @@ struct Engine : EngineBase {
   // is at most 1e-13 of the largest squared column norm depends numerically on
   // them and gives a zero column of Q and a zero row of R. R: k x k row-major
   // FP64, or null.
-  void one_pass(Arena& ar, const T* Y, int64_t m, int k, T* Q, double* R) {
+  // How Q = Y R^-1 is formed in one pass: PASS_PLAIN on the tensor cores (3xTF32 mode);
+  // PASS_CUDA_CORES unbiased on the CUDA cores; PASS_DIAG_SPLIT the diagonal of R^-1 as an
+  // FP32 column scaling (round to nearest) plus the off-diagonal rest on the tensor cores. In
+  // the second pass R is the identity up to the first pass's rounding, so the rest is small
+  // and so is the truncation error of its accumulation: the columns of Q keep unit norm.
+  enum Pass { PASS_PLAIN = 0, PASS_CUDA_CORES = 1, PASS_DIAG_SPLIT = 2 };
+  void one_pass(Arena& ar, const T* Y, int64_t m, int k, T* Q, double* R, int how = PASS_PLAIN) {
     double* G = ar.get_n<double>((int64_t)k * k);
     gram_f64<T>(s, Y, m, k, m, G);
     cholesky_upper_f64(s, G, k, env->d_info, ar.get_n<double>(8));
@@ -498,18 +592,27 @@ struct Engine : EngineBase {
     tri_inverse_upper_f64(s, G, k, Rinv);
     convert_f64_t<T>(s, Rinv, k, k, Bt);   // Rinv is row-major; Bt col-major
     // Q(m, j) = sum_i Y(m, i) Rinv(i, j)
-    mm_right(m, k, k, Y, m, Bt, k, Q, m);
+    if (how == PASS_DIAG_SPLIT) {
+      zero_diag<T>(s, Bt, k, k);
+      mm_right(m, k, k, Y, m, Bt, k, Q, m);
+      add_diag_cols<T>(s, Y, m, k, m, Rinv, k, Q, m);
+    } else {
+      mm_right(m, k, k, Y, m, Bt, k, Q, m, how == PASS_CUDA_CORES ? TALL_CUDA_CORES : TALL_PLAIN);
+    }
     if (R) FP_CUDA(cudaMemcpyAsync(R, G, sizeof(double) * k * k, cudaMemcpyDeviceToDevice, s));
   }
 
+  // Thin QR (CholeskyQR2). The first pass's rounding is absorbed by the second when only Q
+  // is needed; when R is returned too (the singular values come from it) the first pass is
+  // unbiased as well, so that Q R reproduces Y.
   void qr(const T* Y, int64_t m, int k, T* Q, double* R) {
     Phase ph_(this, 1);
     Arena ar = arena();
     T* Q1 = ar.get_n<T>(m * k);
     double* R1 = R ? ar.get_n<double>((int64_t)k * k) : nullptr;
     double* R2 = R ? ar.get_n<double>((int64_t)k * k) : nullptr;
-    one_pass(ar, Y, m, k, Q1, R1);
-    one_pass(ar, Q1, m, k, Q, R2);
+    one_pass(ar, Y, m, k, Q1, R1, R ? PASS_CUDA_CORES : PASS_PLAIN);
+    one_pass(ar, Q1, m, k, Q, R2, PASS_DIAG_SPLIT);
     if (R) {   // R = R2 R1 (row-major)
       gemm_simt<double>(s, k, k, k, 1.0, R2, k, 1, R1, 1, k, 0.0, R, out_rowmajor(k, k, k));
     }
@@ -519,6 +622,9 @@ struct Engine : EngineBase {
   struct Lin {
     int64_t m, n;
     std::function<void(const T*, T*, int64_t)> fwd, bwd;
+    // the last application B^T = A^T Q, whose scale reaches the singular values
+    // (empty: bwd)
+    std::function<void(const T*, T*, int64_t)> bwd_last;
   };
   struct RsvdOut {
     T* Q;        // m x k
@@ -543,7 +649,7 @@ struct Engine : EngineBase {
       A.fwd(Qz, Y, k);
       qr(Y, m, k, r.Q, nullptr);
     }
-    A.bwd(r.Q, Z, k);                       // B^T = A^T Q  (n x k)
+    (A.bwd_last ? A.bwd_last : A.bwd)(r.Q, Z, k);   // B^T = A^T Q  (n x k)
     double* Rb = ar.get_n<double>((int64_t)k * k);
     qr(Z, n, k, Qz, Rb);                    // B^T = Q_b R_b
     // SVD of R_b^T: the row-major R_b array read as col-major is R_b^T
@@ -564,7 +670,7 @@ struct Engine : EngineBase {
     T* Vt = ar.get_n<T>((int64_t)k * k);
     convert_f64<T>(s, Vs, Vt, (int64_t)k * k);
     r.QbW = ar.get_n<T>(n * k);
-    mm_right(n, k, k, Qz, n, Vt, k, r.QbW, n);
+    mm_right(n, k, k, Qz, n, Vt, k, r.QbW, n, TALL_CALIBRATED);
     r.sigma.resize(k);
     FP_CUDA(cudaMemcpyAsync(r.sigma.data(), sg, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     FP_CUDA(cudaStreamSynchronize(s));
@@ -617,7 +723,7 @@ struct Engine : EngineBase {
       Site st = make_site(ar, row, c, true, false);
       FP_CHECK(st.bD == 1, FPEPS_ERR_ARG, "last row must have dimension-1 down legs");
       T* Z = ar.get_n<T>((int64_t)st.bR * st.tp);
-      theta_t(st, v, ones, Z, 1);
+      apply(OP_THETA_T, st, v, ones, Z, 1, true);
       const int64_t n = (int64_t)st.bR * st.tp;
       if (c < Ly - 1) {
         double nrm = host_norm(Z, n);
@@ -744,12 +850,18 @@ struct Engine : EngineBase {
                   scatter_rows<T>(s, Y, nr, dri, nr, kk, fullr, rows);
                   theta_t(st, elc, fullr, fullc, kk);
                   gather_rows<T>(s, fullc, cols, dci, nc, kk, Z, nc);
+                },
+                [&, dri, dci, nr, nc](const T* Y, T* Z, int64_t kk) {   // last application (see the dense zip-up)
+                  FP_CUDA(cudaMemsetAsync(fullr, 0, sizeof(T) * rows * kk, s));
+                  scatter_rows<T>(s, Y, nr, dri, nr, kk, fullr, rows);
+                  apply(OP_THETA_T, st, elc, fullr, fullc, kk, prm.n_fit == 0);
+                  gather_rows<T>(s, fullc, cols, dci, nc, kk, Z, nc);
                 }};
           RsvdOut r = rsvd(ar, A, om, kq[n], prm.power_iters);
           T* Ut = ar.get_n<T>((int64_t)kq[n] * kq[n]);
           convert_f64<T>(s, r.U, Ut, (int64_t)kq[n] * kq[n]);
           Ls[n] = ar.get_n<T>(nr * kq[n]);
-          mm_right(nr, kq[n], kq[n], r.Q, nr, Ut, kq[n], Ls[n], nr);
+          mm_right(nr, kq[n], kq[n], r.Q, nr, Ut, kq[n], Ls[n], nr, TALL_CALIBRATED);
           Rs[n] = r.QbW;
           sig[n] = r.sigma;
           for (double v : r.sigma) tot += v * v;
@@ -819,13 +931,15 @@ struct Engine : EngineBase {
       Env3 elc = EL[c];
       Lin A{rows, cols,
             [&](const T* X, T* Y, int64_t kk) { theta(st, elc, X, Y, kk); },
-            [&](const T* Y, T* Z, int64_t kk) { theta_t(st, elc, Y, Z, kk); }};
+            [&](const T* Y, T* Z, int64_t kk) { theta_t(st, elc, Y, Z, kk); },
+            // without a fit pass the zip-up's singular values set the row's scale
+            [&](const T* Y, T* Z, int64_t kk) { apply(OP_THETA_T, st, elc, Y, Z, kk, prm.n_fit == 0); }};
       RsvdOut r = rsvd(ar, A, omega, k, prm.power_iters);
       // N = Q U[:, :chi_c]
       T* Ut = ar.get_n<T>((int64_t)k * k);
       convert_f64<T>(s, r.U, Ut, (int64_t)k * k);
       T* N = rowmem.get_n<T>(rows * chi_c);
-      mm_right(rows, chi_c, k, r.Q, rows, Ut, k, N, rows);
+      mm_right(rows, chi_c, k, r.Q, rows, Ut, k, N, rows, TALL_CALIBRATED);
       // sign gauge: weights from the sketch generator (stage 2) over the (a, Dn)
       // flat index; rows are stored Dn-major with a fastest
       double* sgn = ar.get_n<double>(chi_c);
@@ -868,7 +982,7 @@ struct Engine : EngineBase {
       fill<T>(s, one, 1, T(1));
       const int64_t rows = (int64_t)EL[c].a * st.bD;
       T* yv = ar.get_n<T>(rows);
-      theta(st, EL[c], one, yv, 1);                                  // [1][Dn][a]
+      apply(OP_THETA, st, EL[c], one, yv, 1, true);                  // [1][Dn][a]
       Nlast = rowmem.get_n<T>(rows);
       permute3<T>(s, yv, Nlast, 1, st.bD, EL[c].a, 0, 2, 1);        // -> [a][Dn][1]
       double nrm = host_norm(Nlast, rows);
@@ -1030,9 +1144,9 @@ struct Engine : EngineBase {
       // expanded right environment and the fitted tensor at c-1 (pattern 2(a))
       const int64_t nER = (int64_t)sl.tp * sl.bR;    // (t_{c-1}, L_c) space
       T* ERp = ar.get_n<T>(nER * j);
-      theta_r(sc, erc, Vp, ERp, j);
+      apply(OP_THETA_R, sc, erc, Vp, ERp, j, true);
       T* Mp = ar.get_n<T>(rows_a * j);
-      theta(sl, elc, ERp, Mp, j);
+      apply(OP_THETA, sl, elc, ERp, Mp, j, true);
       const int keep = (int)std::min<int64_t>({(int64_t)chi, rows_a, (int64_t)j});
       // SVD of M' = Q_m R_m,  R_m = U_r S W^T  (Jacobi on R_m^T: U_jac = W, V_jac = U_r)
       T* Qm = ar.get_n<T>(rows_a * j);
@@ -1055,7 +1169,7 @@ struct Engine : EngineBase {
       convert_f64<T>(s, Vs, Urt, (int64_t)j * j);
       // new right isometry N_c^T = V' W[:, :keep]  ->  [keep][Dn][a_c]
       T* Nc = (T*)e->al.get(sizeof(T) * cols_a * keep);
-      mm_right(cols_a, keep, j, Vp, cols_a, Wt, j, Nc, cols_a);
+      mm_right(cols_a, keep, j, Vp, cols_a, Wt, j, Nc, cols_a, TALL_CALIBRATED);
       double* sgn = ar.get_n<double>(keep);
       T* gw = ar.get_n<T>(cols_a);
       gaussian_sketch<T>(s, gw, cols_a, 1, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16),
@@ -1069,14 +1183,14 @@ struct Engine : EngineBase {
       double* scl = ar.get_n<double>(keep);
       mul_vec(s, sg, sgn, scl, keep);
       T* Mv = ar.get_n<T>(rows_a * keep);
-      mm_right(rows_a, keep, j, Qm, rows_a, Urt, j, Mv, rows_a);
+      mm_right(rows_a, keep, j, Qm, rows_a, Urt, j, Mv, rows_a, TALL_CALIBRATED);
       scale_cols<T>(s, Mv, rows_a, keep, rows_a, scl);
       Arena mnew = arena();
       T* Mnext = mnew.get_n<T>(rows_a * keep);
       permute3<T>(s, Mv, Mnext, keep, Dnl, a2, 2, 1, 0);
       // ER_c vectors = ER' W[:, :keep] diag(sign)  -> [keep][L][t]
       T* erv = ar.get_n<T>(nER * keep);
-      mm_right(nER, keep, j, ERp, nER, Wt, j, erv, nER);
+      mm_right(nER, keep, j, ERp, nER, Wt, j, erv, nER, TALL_CALIBRATED);
       scale_cols<T>(s, erv, nER, keep, nER, sgn);
       double nrm = host_norm(erv, nER * keep);
       FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "right environment vanished");
@@ -1340,9 +1454,9 @@ struct Engine : EngineBase {
       // expanded right environment and the fitted tensor at c-1 (pattern 2(a))
       const int64_t nER = (int64_t)sl.tp * sl.bR;
       T* ERp = ar.get_n<T>(nER * j);
-      theta_r(sc, erc, Vp, ERp, j);
+      apply(OP_THETA_R, sc, erc, Vp, ERp, j, true);
       T* Mp = ar.get_n<T>(rows_a * j);
-      theta(sl, elc, ERp, Mp, j);
+      apply(OP_THETA, sl, elc, ERp, Mp, j, true);
       // SVD of M' per sector (rows: charge of a_{c-1} from the left, columns: of V')
       std::vector<SecIdx> ms = sectors_of(ar, rowq, qVp);
       std::vector<T*> Ls(ms.size()), Ws(ms.size());
@@ -1386,7 +1500,7 @@ struct Engine : EngineBase {
         // tall: B = Q R, R = U_r S W^T -> left Q U_r (nr x rr), right W (ncj x rr);
         // wide: B^T = Q R likewise -> left W (nr x rr), right Q U_r (ncj x rr)
         T* QU = ar.get_n<T>(mm * rr);
-        mm_right(mm, rr, rr, Qm, mm, Urt, rr, QU, mm);
+        mm_right(mm, rr, rr, Qm, mm, Urt, rr, QU, mm, TALL_CALIBRATED);
         Ls[n] = tall ? QU : Wt;
         Ws[n] = tall ? Wt : QU;
         sv[n].resize(rr);
@@ -1420,7 +1534,7 @@ struct Engine : EngineBase {
       }
       // new right isometry N_c^T = V' W  ->  [keep][Dn][a_c]
       T* Nc = (T*)e->al.get(sizeof(T) * cols_a * keep);
-      mm_right(cols_a, keep, j, Vp, cols_a, Wfull, j, Nc, cols_a);
+      mm_right(cols_a, keep, j, Vp, cols_a, Wfull, j, Nc, cols_a, TALL_CUDA_CORES);
       double* sgn = ar.get_n<double>(keep);
       T* gw = ar.get_n<T>(cols_a);
       gaussian_sketch<T>(s, gw, cols_a, 1, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer, (uint64_t)c | (2ull << 16),
@@ -1439,7 +1553,7 @@ struct Engine : EngineBase {
       T* Mnext = mnew.get_n<T>(rows_a * keep);
       permute3<T>(s, Ufull, Mnext, keep, Dnl, a2, 2, 1, 0);
       T* erv = ar.get_n<T>(nER * keep);
-      mm_right(nER, keep, j, ERp, nER, Wfull, j, erv, nER);
+      mm_right(nER, keep, j, ERp, nER, Wfull, j, erv, nER, TALL_CUDA_CORES);
       scale_cols<T>(s, erv, nER, keep, nER, sgn);
       double nrm = host_norm(erv, nER * keep);
       FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "right environment vanished");

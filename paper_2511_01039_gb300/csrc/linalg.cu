@@ -560,6 +560,44 @@ __global__ void k_sumsq(const T* x, int64_t n, double* out) {
 
 __global__ void k_sqrt1(double* x) { x[0] = sqrt(x[0]); }
 
+// out[0] += sum x r, out[1] += sum r r (FP64)
+template <class T>
+__global__ void k_dot2(const T* x, const T* r, int64_t n, double* out) {
+  double a = 0, b = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double xv = (double)x[e], rv = (double)r[e];
+    a = fma(xv, rv, a);
+    b = fma(rv, rv, b);
+  }
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __shared__ double wa[32], wb[32];
+  if (threadIdx.x % 32 == 0) {
+    wa[threadIdx.x / 32] = a;
+    wb[threadIdx.x / 32] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < blockDim.x / 32 ? wa[threadIdx.x] : 0.0;
+    b = threadIdx.x < blockDim.x / 32 ? wb[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(out, a);
+      atomicAdd(out + 1, b);
+    }
+  }
+}
+// out[0] = out[0] / out[1] (1 when the reference is zero or the ratio is not finite)
+__global__ void k_ratio(double* out) {
+  const double r = out[1] > 0 ? out[0] / out[1] : 1.0;
+  out[0] = (isfinite(r) && r > 0) ? r : 1.0;
+}
+
 template <class T>
 __global__ void k_scale_inv(T* x, int64_t n, const double* nrm) {
   const double inv = 1.0 / nrm[0];
@@ -652,6 +690,23 @@ __global__ void k_scale_cols(T* X, int64_t m, int n, int64_t ld, const double* s
     int64_t j = e / m, i = e % m;
     X[j * ld + i] = (T)((double)X[j * ld + i] * sc[j]);
   }
+}
+
+// out(i, j) = X(i, j) * d_j + out(i, j) with d_j = R[j * k + j] (the diagonal of a
+// row-major FP64 k x k matrix), one FP32 (or FP64) fused multiply-add per element
+template <class T>
+__global__ void k_add_diag_cols(const T* X, int64_t m, int n, int64_t ldx, const double* R, int k, T* out,
+                                int64_t ldo) {
+  const int64_t tot = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e % m;
+    out[j * ldo + i] = fma(X[j * ldx + i], (T)R[j * (int64_t)k + j], out[j * ldo + i]);
+  }
+}
+template <class T>
+__global__ void k_zero_diag(T* A, int k, int64_t ld) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) A[j * ld + j] = T(0);
 }
 
 __global__ void k_mul_vec(const double* a, const double* b, double* out, int n) {
@@ -831,6 +886,15 @@ void frob_norm_f64(cudaStream_t s, const T* x, int64_t n, double* out) {
 }
 
 template <class T>
+void scale_against(cudaStream_t s, const T* x, const T* r, int64_t n, double* out) {
+  FP_CUDA(cudaMemsetAsync(out, 0, 2 * sizeof(double), s));
+  k_dot2<T><<<grid_for(n), 256, 0, s>>>(x, r, n, out);
+  FP_LAUNCH();
+  k_ratio<<<1, 1, 0, s>>>(out);
+  FP_LAUNCH();
+}
+
+template <class T>
 void scale_by_inv(cudaStream_t s, T* x, int64_t n, const double* nrm) {
   k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(x, n, nrm);
   FP_LAUNCH();
@@ -849,6 +913,20 @@ void transpose_pad(cudaStream_t s, const T* src, int64_t rows, int64_t cols, int
   const int64_t gy = (ld_dst + 31) / 32, gx = (cols + 31) / 32;
   FP_CHECK(gy < 65536, FPEPS_ERR_UNSUPPORTED, "transpose: too many rows");
   k_transpose_pad<T><<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(src, rows, cols, ld_src, dst, ld_dst);
+  FP_LAUNCH();
+}
+
+template <class T>
+void add_diag_cols(cudaStream_t s, const T* X, int64_t m, int n, int64_t ldx, const double* R, int k, T* out,
+                   int64_t ldo) {
+  if (m * n == 0) return;
+  k_add_diag_cols<T><<<grid_for(m * n), 256, 0, s>>>(X, m, n, ldx, R, k, out, ldo);
+  FP_LAUNCH();
+}
+template <class T>
+void zero_diag(cudaStream_t s, T* A, int k, int64_t ld) {
+  if (k <= 0) return;
+  k_zero_diag<T><<<(k + 255) / 256, 256, 0, s>>>(A, k, ld);
   FP_LAUNCH();
 }
 
@@ -969,10 +1047,13 @@ void transpose_block(cudaStream_t s, const T* src, int64_t lds, int64_t rows, in
   template void to_f64<T>(cudaStream_t, const T*, double*, int64_t);                                          \
   template void frob_norm_f64<T>(cudaStream_t, const T*, int64_t, double*);                                  \
   template void scale_by_inv<T>(cudaStream_t, T*, int64_t, const double*);                                   \
+  template void scale_against<T>(cudaStream_t, const T*, const T*, int64_t, double*);                        \
   template void permute3<T>(cudaStream_t, const T*, T*, int64_t, int64_t, int64_t, int, int, int);            \
   template void transpose_pad<T>(cudaStream_t, const T*, int64_t, int64_t, int64_t, T*, int64_t);            \
   template void sub_into<T>(cudaStream_t, T*, const T*, const T*, int64_t);                                   \
   template void convert_f64_t<T>(cudaStream_t, const double*, int64_t, int64_t, T*);                         \
+  template void add_diag_cols<T>(cudaStream_t, const T*, int64_t, int, int64_t, const double*, int, T*, int64_t); \
+  template void zero_diag<T>(cudaStream_t, T*, int, int64_t);                                                 \
   template void fill<T>(cudaStream_t, T*, int64_t, T);                                                        \
   template void check_finite<T>(cudaStream_t, const T*, int64_t, int*);                                      \
   template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, const T*, double*);                         \

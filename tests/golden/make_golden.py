@@ -5,8 +5,11 @@ Configurations (seeded synthetic inputs, no paper data):
                 oversample 10, q=2, n_fit=1: <psi|H|psi> (layer 1) and <psi|psi> (layer 0).
   c2_fsm_decay  the same with the decaying-bond-weight PEPS (exp(-i/2) on every
                 virtual index), whose bond spectra are well separated.
-Usage: python tests/golden/make_golden.py [--decay] [seeds...]
-       -> tests/golden/c2_fsm[_decay]_seed{S}.json
+  c3_fsm[_decay] 6x6, D=6, p=4, FSM PEPO w=4 (K=2, random symmetric h, X, Y), chi=256,
+                oversample 10, q=2, n_fit=1: <psi|H|psi> and <psi|psi> by full sweeps,
+                the log-scale of every compressed row and the kept spectra of row 2.
+Usage: python tests/golden/make_golden.py [--decay] [--c3] [seeds...]
+       -> tests/golden/c2_fsm[_decay]_seed{S}.json, c3_fsm[_decay]_seed{S}.json
 """
 import json
 import os
@@ -39,14 +42,40 @@ def c2(seed: int, sketch_seed: int = 1, decay: bool = False):
     }
 
 
+def c3(seed: int, sketch_seed: int = 1, decay: bool = False):
+    peps = (L.decaying_peps if decay else L.random_peps)(6, 6, 6, 4, seed=seed)
+    ham = L.random_hamiltonian(6, 6, 4, 2, seed=seed)
+    pepo = L.fsm_pepo(ham)
+    prm = B.RsvdParams(oversample=10, power_iters=2, n_fit=1)
+    t0 = time.time()
+    sn, ln, rows_n = B.contract(peps, pepo, 256, prm, seed=sketch_seed, layer=1, return_rows=True)
+    t1 = time.time()
+    sd, ld, rows_d = B.contract(peps, L.identity_pepo(6, 6, 4), 256, prm, seed=sketch_seed, layer=0,
+                                return_rows=True)
+    return {
+        "config": "6x6 D=6 p=4 FSM w=4 (K=2) chi=256 oversample=10 q=2 n_fit=1" + (" decaying PEPS" if decay else ""),
+        "decay": decay,
+        "peps_seed": seed, "ham_seed": seed, "sketch_seed": sketch_seed,
+        "num_sign": sn, "num_log": ln, "den_sign": sd, "den_log": ld,
+        "row_log_scale_layer1": [float(r.log_scale) for r in rows_n],
+        "row_log_scale_layer0": [float(r.log_scale) for r in rows_d],
+        "zip_spectra_row2_layer1": [list(map(float, s)) for s in rows_n[1].zip_spectra],
+        "fit_spectra_row2_layer1": [list(map(float, s)) for s in rows_n[1].fit_spectra],
+        "oracle_seconds_layer1": t1 - t0,
+        "oracle_seconds": time.time() - t0,
+    }
+
+
 if __name__ == "__main__":
     here = os.path.dirname(os.path.abspath(__file__))
     args = sys.argv[1:]
     decay = "--decay" in args
-    args = [a for a in args if a != "--decay"]
+    big = "--c3" in args
+    args = [a for a in args if a not in ("--decay", "--c3")]
     for s in [int(x) for x in (args or ["0"])]:
-        out = c2(s, decay=decay)
-        name = f"c2_fsm_decay_seed{s}.json" if decay else f"c2_fsm_seed{s}.json"
+        out = (c3 if big else c2)(s, decay=decay)
+        stem = "c3_fsm" if big else "c2_fsm"
+        name = f"{stem}_decay_seed{s}.json" if decay else f"{stem}_seed{s}.json"
         with open(os.path.join(here, name), "w") as f:
             json.dump(out, f, indent=1)
         print(s, out["num_log"], out["den_log"], out["oracle_seconds"])
