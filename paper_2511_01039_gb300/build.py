@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["abi.cu", "engine.cu", "gemm_simt.cu", "gemm_tc.cu", "sandwich.cu", "linalg.cu", "svd_noalloc.cu"]
+SOURCES = ["abi.cu", "engine.cu", "gemm_simt.cu", "gemm_tc.cu", "sandwich.cu", "sandwich_tc.cu", "linalg.cu",
+           "svd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -103,6 +103,18 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
 size_t gemm_tc_scratch_bytes(int mode, int64_t M, int64_t N, int64_t K);
 
 // ---------------------------------------------------------------- sandwich
+// Bundle order. A (ket, PEPO, bra) bundle of dims (n, nw, n) is indexed (x nw + x_w) n + x'
+// everywhere except in the output of the sandwich, where the output bundle with unit stride
+// (the one the next GEMM contracts over) is stored PEPO-index outermost, (x_w n + x) n + x':
+// one output pair (v_w, z_w) then owns contiguous runs of n^2 elements. The operand that
+// the next GEMM contracts with that bundle is stored in the same order (bundle_outer).
+__host__ __device__ inline int64_t bundle_index(int x, int xw, int xp, int n, int nw, bool pepo_outer) {
+  return pepo_outer ? ((int64_t)xw * n + x) * n + xp : ((int64_t)x * nw + xw) * n + xp;
+}
+// out[r][(x_w n + x) n + x'] = in[r][(x nw + x_w) n + x'] for r < rows
+template <class T>
+void bundle_outer(cudaStream_t s, const T* in, T* out, int64_t rows, int n, int nw);
+
 // One orientation of the site sandwich: inputs legs (x, y) -> outputs (v, z).
 struct SandOrient {
   int nx, nxw, ny, nyw, nv, nvw, nz, nzw, p;
@@ -112,6 +124,9 @@ struct SandOrient {
   const void* d_aw;        // [nch][nx][ny][nv][nz][p']  (A . W_ch)
   const void* d_ar;        // [nx][ny][nv][nz][p]        (A in these roles)
   int ch_host_max_per_pair;
+  // tcgen05 sandwich (FP32 data): hi/lo operand images of A . W_ch and of the bra
+  const void* d_kimg = nullptr;
+  const void* d_arimg = nullptr;
 };
 
 template <class T>
@@ -124,6 +139,17 @@ bool sandwich_mma_fits(const SandOrient& o);
 void sandwich_apply_tc(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const float* in, int64_t i_t,
                        int64_t i_k, int64_t i_X, int64_t i_Y, float* out, int64_t o_t, int64_t o_k, int64_t o_V,
                        int64_t o_Z);
+
+// tcgen05 3xTF32 version (sandwich_tc.cu), float data; needs D <= 6, p <= 4 and p D^2 <= 144.
+// The operand images are built once per site and orientation (sandwich_tc_images, sizes from
+// sandwich_tc_image_floats); err is the tensor-core error word (set to 1 when a bounded wait
+// timed out).
+bool sandwich_tc_fits(const SandOrient& o);
+void sandwich_tc_image_floats(const SandOrient& o, size_t* ket, size_t* bra);
+void sandwich_tc_images(cudaStream_t s, const SandOrient& o, float* ket_img, float* bra_img);
+void sandwich_apply_tcgen05(cudaStream_t s, const SandOrient& o, int64_t nt, int64_t nk, const float* in,
+                            int64_t i_t, int64_t i_k, int64_t i_X, int64_t i_Y, float* out, int64_t o_t, int64_t o_k,
+                            int64_t o_V, int64_t o_Z, int* err);
 
 // Builds the role-permuted ket and the channel products A.W_ch for one orientation.
 // roles[4] = leg index (0..3 = l,u,r,d) of (x, y, v, z).

@@ -116,6 +116,17 @@ void ensure_sandwich(fpeps_env* env, int layer, int row) {
       so.d_pair_off = d_off;
       so.d_aw = d_aw;
       so.d_ar = d_ar;
+      if (env->elem == 4 && sandwich_tc_fits(so)) {   // operand images of the tcgen05 sandwich
+        size_t nk = 0, nb = 0;
+        sandwich_tc_image_floats(so, &nk, &nb);
+        void* ki = env->al.get(nk * sizeof(float));
+        void* bi = env->al.get(nb * sizeof(float));
+        sd.bufs.push_back(ki);
+        sd.bufs.push_back(bi);
+        sandwich_tc_images(env->stream, so, (float*)ki, (float*)bi);
+        so.d_kimg = ki;
+        so.d_arimg = bi;
+      }
       sd.o[o] = so;
       // keep the host copy alive until the copies above have executed
       FP_CUDA(cudaStreamSynchronize(env->stream));
@@ -308,6 +319,7 @@ struct Engine : EngineBase {
   struct Site {
     int c = 0, t = 1, tp = 1;
     int bL = 1, bU = 1, bR = 1, bD = 1;
+    int nA[4] = {1, 1, 1, 1}, nW[4] = {1, 1, 1, 1};   // ket and PEPO dims of the legs l, u, r, d
     const T *Tm = nullptr, *Tt = nullptr, *Tp = nullptr, *Tq = nullptr;
     const SiteSand* sd = nullptr;
   };
@@ -317,11 +329,28 @@ struct Engine : EngineBase {
     const T* Et = nullptr;
   };
 
-  // the sandwich step: tensor cores (3xTF32, mma.sync) in the split-precision
-  // modes when the site fits the tile, CUDA cores otherwise
+  // error word of the tensor-core kernels (first int of tc_scr)
+  int* tc_err() {
+    if (!tc_scr) {
+      tc_scr = env->al.get(256);
+      tc_n = 256;
+      FP_CUDA(cudaMemsetAsync(tc_scr, 0, sizeof(int), s));
+    }
+    tc_used = true;
+    return (int*)tc_scr;
+  }
+
+  // the sandwich step: tcgen05 tensor cores (3xTF32) in the split-precision modes
+  // when the site fits the tile, CUDA cores otherwise
   void sandwich(const SandOrient& o, int64_t nt, int64_t nk, const T* in, int64_t i_t, int64_t i_k, int64_t i_X,
                 int64_t i_Y, T* out, int64_t o_t, int64_t o_k, int64_t o_V, int64_t o_Z) {
-    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && !simt_only && sandwich_mma_fits(o)) {
+    const bool split = sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && !simt_only;
+    if (split && o.d_kimg && sandwich_tc_fits(o)) {
+      sandwich_apply_tcgen05(s, o, nt, nk, (const float*)in, i_t, i_k, i_X, i_Y, (float*)out, o_t, o_k, o_V, o_Z,
+                             tc_err());
+      return;
+    }
+    if (split && sandwich_mma_fits(o)) {
       sandwich_apply_tc(s, o, nt, nk, (const float*)in, i_t, i_k, i_X, i_Y, (float*)out, o_t, o_k, o_V, o_Z);
       return;
     }
@@ -524,6 +553,10 @@ struct Engine : EngineBase {
     st.c = c;
     const SiteHost& h = env->sites[env->layer][row * env->cfg.Ly + c];
     st.bL = bund(h, 0); st.bU = bund(h, 1); st.bR = bund(h, 2); st.bD = bund(h, 3);
+    for (int l = 0; l < 4; ++l) {
+      st.nA[l] = h.dA[l];
+      st.nW[l] = h.dW[l];
+    }
     st.t = env->tb[c];
     st.tp = env->tb[c + 1];
     FP_CHECK(env->tphys[c] == st.bU, FPEPS_ERR_ARG, "boundary bundle does not match the row's up legs");
@@ -531,15 +564,20 @@ struct Engine : EngineBase {
     const T* Tm = (const T*)env->T[c];
     st.Tm = Tm;
     const int64_t t = st.t, U = st.bU, tp = st.tp;
+    // Tt and Tp meet the sandwich output's unit-stride bundle (U) in the GEMM after the
+    // sandwich: their U index is PEPO-outermost like that output (see bundle_index)
+    T* tmp = (need_fwd || need_r) ? ar.get_n<T>(t * U * tp) : nullptr;
     if (need_fwd) {
       T* Tt = ar.get_n<T>(t * U * tp);
-      permute3<T>(s, Tm, Tt, t, U, tp, 2, 0, 1);
+      permute3<T>(s, Tm, tmp, t, U, tp, 2, 0, 1);
+      bundle_outer<T>(s, tmp, Tt, tp * t, h.dA[1], h.dW[1]);
       st.Tt = Tt;
     }
     if (need_r) {
       T* Tp = ar.get_n<T>(t * U * tp);
       T* Tq = ar.get_n<T>(t * U * tp);
-      permute3<T>(s, Tm, Tp, t, U, tp, 0, 2, 1);
+      permute3<T>(s, Tm, tmp, t, U, tp, 0, 2, 1);
+      bundle_outer<T>(s, tmp, Tp, t * tp, h.dA[1], h.dW[1]);
       permute3<T>(s, Tm, Tq, t, U, tp, 2, 1, 0);
       st.Tp = Tp;
       st.Tq = Tq;
@@ -547,13 +585,18 @@ struct Engine : EngineBase {
     return st;
   }
 
-  // env tensors from a vector block V[a][bundle][bond] (a vectors): E [a][bond][bundle], Et [bond][bundle][a]
-  Env3 env_from_vectors(Arena& ar, const T* Vb, int a, int64_t bundle, int64_t bond) {
+  // env tensors from a vector block V[a][bundle][bond] (a vectors): E [a][bond][bundle], Et
+  // [bond][bundle][a]. E meets the sandwich output in the GEMM after the sandwich, so its bundle
+  // (ket dim n, PEPO dim nw) is stored PEPO-outermost like that output (see bundle_index).
+  Env3 env_from_vectors(Arena& ar, const T* Vb, int a, int64_t bundle, int64_t bond, int n, int nw) {
     Env3 e;
     e.a = a;
     T* E = ar.get_n<T>((int64_t)a * bundle * bond);
     T* Et = ar.get_n<T>((int64_t)a * bundle * bond);
-    permute3<T>(s, Vb, E, a, bundle, bond, 0, 2, 1);
+    Arena tmp = arena();
+    T* En = tmp.get_n<T>((int64_t)a * bundle * bond);
+    permute3<T>(s, Vb, En, a, bundle, bond, 0, 2, 1);
+    bundle_outer<T>(s, En, E, (int64_t)a * bond, n, nw);
     permute3<T>(s, Vb, Et, a, bundle, bond, 2, 1, 0);
     e.E = E;
     e.Et = Et;
@@ -731,7 +774,7 @@ struct Engine : EngineBase {
         scale_by_inv<T>(s, Z, n, e->d_scal);
         log_s += std::log(nrm);
         Arena nk = arena();
-        Env3 nv = env_from_vectors(nk, Z, 1, st.bR, st.tp);
+        Env3 nv = env_from_vectors(nk, Z, 1, st.bR, st.tp, st.nA[2], st.nW[2]);
         FP_CUDA(cudaStreamSynchronize(s));
         keep.reset();
         keep.live = nk.live;   // transfer ownership
@@ -918,7 +961,7 @@ struct Engine : EngineBase {
         Nvec[c] = N;
         abond[c + 1] = chi_c;
         ELvec[c + 1] = elv;
-        EL[c + 1] = env_from_vectors(rowmem, elv, chi_c, st.bR, st.tp);
+        EL[c + 1] = env_from_vectors(rowmem, elv, chi_c, st.bR, st.tp, st.nA[2], st.nW[2]);
         FP_CUDA(cudaStreamSynchronize(s));
         continue;
       }
@@ -969,7 +1012,7 @@ struct Engine : EngineBase {
       Nvec[c] = N;
       abond[c + 1] = chi_c;
       ELvec[c + 1] = elv;
-      EL[c + 1] = env_from_vectors(rowmem, elv, chi_c, st.bR, st.tp);
+      EL[c + 1] = env_from_vectors(rowmem, elv, chi_c, st.bR, st.tp, st.nA[2], st.nW[2]);
       FP_CUDA(cudaStreamSynchronize(s));
     }
     // last site: Theta has a single column
@@ -1198,7 +1241,7 @@ struct Engine : EngineBase {
       rs_M = rs;
       rs += std::log(nrm);
       Arena ernew = arena();
-      Env3 ERn = env_from_vectors(ernew, erv, keep, sl.bR, sl.tp);
+      Env3 ERn = env_from_vectors(ernew, erv, keep, sl.bR, sl.tp, sl.nA[2], sl.nW[2]);
       {
         std::vector<double> sv(j);
         FP_CUDA(cudaMemcpyAsync(sv.data(), sg, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
@@ -1561,7 +1604,7 @@ struct Engine : EngineBase {
       rs_M = rs;
       rs += std::log(nrm);
       Arena ernew = arena();
-      Env3 ERn = env_from_vectors(ernew, erv, keep, sl.bR, sl.tp);
+      Env3 ERn = env_from_vectors(ernew, erv, keep, sl.bR, sl.tp, sl.nA[2], sl.nW[2]);
       e->spectra.fit[c - 1] = skeep;
       qright = qk;
       qout[c] = qk;
@@ -1604,7 +1647,9 @@ struct Engine : EngineBase {
     FP_CUDA(cudaMemcpyAsync(elv, el, sizeof(T) * a * t * L, cudaMemcpyHostToDevice, s));
     Env3 E;
     E.a = a;
-    E.E = elv;
+    T* elo = ar.get_n<T>((int64_t)a * t * L);   // L PEPO-outermost (see env_from_vectors)
+    bundle_outer<T>(s, elv, elo, (int64_t)a * t, st.nA[0], st.nW[0]);
+    E.E = elo;
     T* Et = ar.get_n<T>((int64_t)a * t * L);
     permute3<T>(s, elv, Et, a, t, L, 1, 2, 0);
     E.Et = Et;

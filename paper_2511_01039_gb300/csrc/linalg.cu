@@ -704,6 +704,16 @@ __global__ void k_add_diag_cols(const T* X, int64_t m, int n, int64_t ldx, const
   }
 }
 template <class T>
+__global__ void k_bundle_outer(const T* __restrict__ in, T* __restrict__ out, int64_t rows, int n, int nw) {
+  const int B = n * nw * n;
+  const int64_t tot = rows * B;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / B;
+    const int i = (int)(e % B), xp = i % n, xw = (i / n) % nw, x = i / (n * nw);
+    out[r * B + ((int64_t)xw * n + x) * n + xp] = in[e];
+  }
+}
+template <class T>
 __global__ void k_zero_diag(T* A, int k, int64_t ld) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < k) A[j * ld + j] = T(0);
@@ -924,6 +934,13 @@ void add_diag_cols(cudaStream_t s, const T* X, int64_t m, int n, int64_t ldx, co
   FP_LAUNCH();
 }
 template <class T>
+void bundle_outer(cudaStream_t s, const T* in, T* out, int64_t rows, int n, int nw) {
+  const int64_t tot = rows * n * nw * n;
+  if (tot == 0) return;
+  k_bundle_outer<T><<<grid_for(tot), 256, 0, s>>>(in, out, rows, n, nw);
+  FP_LAUNCH();
+}
+template <class T>
 void zero_diag(cudaStream_t s, T* A, int k, int64_t ld) {
   if (k <= 0) return;
   k_zero_diag<T><<<(k + 255) / 256, 256, 0, s>>>(A, k, ld);
@@ -1054,6 +1071,7 @@ void transpose_block(cudaStream_t s, const T* src, int64_t lds, int64_t rows, in
   template void convert_f64_t<T>(cudaStream_t, const double*, int64_t, int64_t, T*);                         \
   template void add_diag_cols<T>(cudaStream_t, const T*, int64_t, int, int64_t, const double*, int, T*, int64_t); \
   template void zero_diag<T>(cudaStream_t, T*, int, int64_t);                                                 \
+  template void bundle_outer<T>(cudaStream_t, const T*, T*, int64_t, int, int);                               \
   template void fill<T>(cudaStream_t, T*, int64_t, T);                                                        \
   template void check_finite<T>(cudaStream_t, const T*, int64_t, int*);                                      \
   template void col_signs<T>(cudaStream_t, const T*, int64_t, int, int64_t, const T*, double*);                         \

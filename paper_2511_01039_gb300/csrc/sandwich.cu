@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
   const T* I = in + t * i_t + k * i_k;
   T* O = out + t * o_t + k * o_k;
   const int tid = threadIdx.x;
+  const bool pv = o_V == 1, pz = o_Z == 1 && o_V != 1;   // the unit-stride output bundle: PEPO outermost
 
   for (int e = tid; e < nacc; e += blockDim.x) ar[e] = AR[e];
 
@@ -133,8 +134,8 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
       if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
         for (int e = tid; e < nv * nv * nz * nz; e += blockDim.x) {
           int zp = e % nz, z = (e / nz) % nz, vp = (e / (nz * nz)) % nv, v = e / (nz * nz * nv);
-          int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp;
-          int64_t Z = ((int64_t)z * o.nzw + zw) * nz + zp;
+          const int64_t V = bundle_index(v, vw, vp, nv, o.nvw, pv);
+          const int64_t Z = bundle_index(z, zw, zp, nz, o.nzw, pz);
           O[V * o_V + Z * o_Z] = T(0);
         }
         continue;
@@ -175,8 +176,8 @@ __global__ void __launch_bounds__(256) k_sandwich(SandOrient o, int64_t nk, cons
             const T* br = ar + ((xp * ny + yp) * nv + vp) * nz * p + zp * p;
             for (int q = 0; q < p; ++q) s += ac[q] * br[q];
           }
-        int64_t V = ((int64_t)v * o.nvw + vw) * nv + vp;
-        int64_t Z = ((int64_t)z * o.nzw + zw) * nz + zp;
+        const int64_t V = bundle_index(v, vw, vp, nv, o.nvw, pv);
+        const int64_t Z = bundle_index(z, zw, zp, nz, o.nzw, pz);
         O[V * o_V + Z * o_Z] = s;
       }
       __syncthreads();
@@ -279,6 +280,10 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
   const int mg = warp / 3, ng = warp % 3;
   const int64_t nblk = nt * nk;
   const bool aw16 = (N1 % 4) == 0 && ((uintptr_t)AW % 16) == 0;
+  // output strides of v, v_w (z, z_w): the unit-stride output bundle is PEPO-index outermost
+  const bool pv = o_V == 1, pz = o_Z == 1 && o_V != 1;
+  const int64_t sv = pv ? nv : (int64_t)o.nvw * nv, swv = pv ? (int64_t)nv * nv : nv;
+  const int64_t sz = pz ? nz : (int64_t)o.nzw * nz, swz = pz ? (int64_t)nz * nz : nz;
 
   // this thread's gather slot: bra position (x', y'), lanes along the contiguous one
   const int gstep = SM_THREADS / K1, gslot = tid % K1, g0 = tid / K1;
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
     for (int e = tid; e < M2; e += SM_THREADS) {
       const int bi = e / N2, vz = e % N2, v = vz / nz, z = vz % nz;
       const int64_t b = b0 + bi, t = b / nk, k = b % nk;
-      rowOut[e] = t * o_t + k * o_k + (int64_t)v * o.nvw * nv * o_V + (int64_t)z * o.nzw * nz * o_Z;
+      rowOut[e] = t * o_t + k * o_k + (int64_t)v * sv * o_V + (int64_t)z * sz * o_Z;
     }
     __syncthreads();
 
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_sandwich_mma(SandOrient o, in
         const int vw = v_fast ? pi : po, zw = v_fast ? po : pi;
         const int pair = vw * o.nzw + zw;
         const int c0 = o.d_pair_off[pair], c1 = o.d_pair_off[pair + 1];
-        const int64_t obase = (int64_t)vw * nv * o_V + (int64_t)zw * nz * o_Z + wpart;
+        const int64_t obase = (int64_t)vw * swv * o_V + (int64_t)zw * swz * o_Z + wpart;
         if (c0 == c1) {   // no PEPO channel feeds this output pair: zeros
           if (wact)
             for (int e = w0; e < M2; e += wstep) out[rowOut[e] + obase] = 0.f;
