@@ -3,11 +3,16 @@
 to chi by zip-up rSVD plus one CBE fit pass, on the 8x8, D=6, w=6
 (Hubbard-shaped FSM PEPO), chi=500 workload, central row r=4.
 
-One step = fpeps_import_boundary (device-resident seeded boundary of rows 0-3)
-+ fpeps_absorb_row(4) + fpeps_compress_rsvd. The metric is algorithmic
-TFLOP/s of the contractions (the Fig. 2(a) applications; QR/SVD flops are not
-counted), the e2e number the same through host buffers (H2D of the boundary,
-D2H of the new boundary inside the timed region).
+One step = fpeps_import_boundary (device-resident checkpoint of rows 0-3)
++ fpeps_absorb_row(4) + fpeps_compress_rsvd. The checkpoint is made once, before
+timing, by sweeping rows 0-3 of the same seeded lattice through the library
+(--boundary random: a seeded random boundary of the same bond profile instead).
+The metric is algorithmic TFLOP/s of the contractions (the Fig. 2(a)
+applications; QR/SVD flops are not counted), the e2e number the same through
+host buffers (H2D of the boundary, D2H of the new boundary inside the timed
+region). The line also carries the plain FP32 path on the same row
+(fp32_path) and the relative errors of norm and energy against the stored FP64
+oracle values of the 6x6, D=6, chi=256 lattice (rel_err_vs_fp64).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|f32|f64]
   python bench.py --impl reference ...   (the FP64 oracle on the host cores)
@@ -44,6 +49,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--boundary", default="sweep", choices=["sweep", "random"],
+                    help="input boundary of the timed row: rows 0..row-1 swept by the library (default), or "
+                         "a seeded random boundary of the same bond profile")
+    ap.add_argument("--fp32-steps", type=int, default=1,
+                    help="timed steps of the plain FP32 path on the same row (0: skip)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the 6x6 chi=256 comparison with the stored FP64 oracle values")
     ap.add_argument("--full-sweep", action="store_true",
                     help="time one full <psi|H|psi> / <psi|psi> evaluation of the 8x8 lattice (every row "
                          "absorbed and compressed, both layers) and print one JSON line, then exit")
@@ -270,6 +282,67 @@ def full_sweep(prec: str):
                       "energy": val, "num_sign": sn, "num_log": ln}), flush=True)
 
 
+# ----------------------------------------------------------------------------- inputs and sub-records
+def sweep_checkpoint(fp, env, row: int, prm) -> bytes:
+    """Checkpoint of the boundary after rows 0..row-1 of the operator layer, made by the
+    library itself (row 0 exact, rows 1..row-1 compressed with `prm`)."""
+    for r in range(row):
+        fp.fpeps_absorb_row(env.h, r, 1)
+        if r > 0:
+            fp.fpeps_compress_rsvd(env.h, prm)
+    return fp.fpeps_export_boundary(env.h)
+
+
+def timed_steps(fp, env, blob_ptr, nbytes, row, prm, steps):
+    """`steps` row steps (import, absorb, compress) between CUDA events on the env stream:
+    (milliseconds, algorithmic flops)."""
+    import torch
+    lib = fp.lib()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(env.stream)
+    flops = 0.0
+    for _ in range(steps):
+        fp._check(env.h, lib.fpeps_import_boundary(env.h, blob_ptr, nbytes, row, 1))
+        fp.fpeps_absorb_row(env.h, row, 1)
+        flops += fp.fpeps_compress_rsvd(env.h, prm).alg_flops
+    e1.record(env.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), flops
+
+
+def accuracy_record(precs=("tf32x3", "f32")):
+    """Relative errors of <psi|H|psi>, <psi|psi> and <H> of the 6x6, D=6, w=4, chi=256 lattice
+    (full sweeps, zip-up rSVD + CBE fit) against the stored FP64 oracle values
+    (tests/golden/c3_fsm_seed0.json, written by tests/golden/make_golden.py), per precision."""
+    import math
+
+    from paper_2511_01039_gb300 import fpeps as fp
+    from synth import lattice as L
+    path = os.path.join(ROOT, "tests", "golden", "c3_fsm_seed0.json")
+    if not os.path.exists(path):
+        return None
+    gold = json.load(open(path))
+    peps = L.random_peps(6, 6, 6, 4, seed=gold["peps_seed"])
+    pepo = L.fsm_pepo(L.random_hamiltonian(6, 6, 4, 2, seed=gold["ham_seed"]))
+    e_ref = gold["num_sign"] * gold["den_sign"] * math.exp(gold["num_log"] - gold["den_log"])
+    out = {"workload": gold["config"], "reference": "FP64 oracle (numpy), stored", "by_precision": {}}
+    for prec in precs:
+        env = fp.Env(peps, pepo, D=6, p=4, w=4, chi=256, prec=prec, seed=gold["sketch_seed"])
+        t0 = time.perf_counter()
+        val, sn, ln = env.expect(fp.params(10, 2, 0, 1, 0))   # operator sweep, then the norm sweep
+        el = time.perf_counter() - t0
+        sd, ld = fp.fpeps_sweep_value(env.h)                    # the norm sweep's value
+        env.close()
+        out["by_precision"][prec] = {
+            "norm": abs(math.exp(ld - gold["den_log"]) - 1) if sd == gold["den_sign"] else 2.0,
+            "numerator": abs(math.exp(ln - gold["num_log"]) - 1) if sn == gold["num_sign"] else 2.0,
+            "energy": abs(val / e_ref - 1),
+            "seconds_both_sweeps": el}
+    return out
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -322,7 +395,10 @@ def main():
     elem = 8 if args.prec == "f64" else 4
     env = fp.Env(wl.peps, wl.pepo, D=wl.D, p=wl.p, w=wl.w, chi=wl.chi, prec=args.prec, seed=1 + rank)
     prm = fp.params(oversample=10, power_iters=2, chi_tilde=0, n_fit=1, exact_svd=0)
-    blob = WL.boundary_blob(wl.boundary, wl.row, 1, elem)
+    if args.boundary == "sweep":
+        blob = sweep_checkpoint(fp, env, wl.row, prm)
+    else:
+        blob = WL.boundary_blob(wl.boundary, wl.row, 1, elem)
     dblob = torch.frombuffer(bytearray(blob), dtype=torch.uint8).to(dev)   # resident checkpoint
     stream = env.stream
 
@@ -395,17 +471,46 @@ def main():
                     "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
                     "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None} for k, v in prof.items()}
 
+    # the headline value against the tensor-core peak (TF32 = measured BF16 x 1.1/2.25; 3xTF32
+    # issues three MMAs per algorithmic product, so its ceiling is a third of that)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tf32 = bf16 * 1.1 / 2.25
+    row_tc = {"tflops": value, "tf32_peak": tf32, "frac_tf32_peak": value / tf32,
+              "frac_3xtf32_ceiling": value / (tf32 / 3.0),
+              "note": ("of measured" if peaks else "of fallback") + " BF16 x 1.1/2.25; whole row incl. QR/SVD time"}
+
+    # ---------------- the plain FP32 path on the same row
+    fp32 = None
+    if args.fp32_steps > 0 and args.prec == "tf32x3" and rank == 0:
+        env32 = fp.Env(wl.peps, wl.pepo, D=wl.D, p=wl.p, w=wl.w, chi=wl.chi, prec="f32", seed=1 + rank)
+        ms32, fl32 = timed_steps(fp, env32, dblob.data_ptr(), len(blob), wl.row, prm, args.fp32_steps)
+        env32.close()
+        fp32 = {"seconds_per_row": ms32 / args.fp32_steps / 1e3, "value": fl32 / (ms32 * 1e-3) / 1e12,
+                "unit": "TFLOP/s", "steps": args.fp32_steps, "warmup": 0,
+                "note": "CUDA-core FP32 GEMMs and sandwich, FP64-class QR/SVD; same row, same input boundary",
+                "mixed_speedup": (ms32 / args.fp32_steps) / (ms / args.steps)}
+
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world if dist else args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "seconds_per_row": ms / args.steps / 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 data, 3xTF32 tensor-core products" if args.prec == "tf32x3" else args.prec,
-            "data": "synthetic (seeded PEPS, Hubbard-shaped PEPO, random boundary)",
+            "data": "synthetic (seeded PEPS, Hubbard-shaped PEPO; input boundary " +
+                    ("swept from rows 0-3 of the same lattice by the library)" if args.boundary == "sweep"
+                     else "seeded random)"),
             "config": {"workload": WORKLOAD, "precision": args.prec, "l2": "inputs and intermediates >> 129 MB L2",
+                       "input_boundary": args.boundary,
                        "parallelism": f"replicas x{world}" if dist else "1 GPU",
                        "alg_flops_per_step": flops / args.steps},
-            "roofline": roof, "kernels": per_kind, "gpu_launches": launches, "clocks": clk.summary()}
+            "roofline": roof, "row_tensor": row_tc, "kernels": per_kind, "gpu_launches": launches,
+            "clocks": clk.summary()}
     if e2e:
         line["e2e"] = e2e
+    if fp32:
+        line["fp32_path"] = fp32
+    if not args.no_accuracy and rank == 0 and args.prec == "tf32x3":
+        acc = accuracy_record()
+        if acc:
+            line["rel_err_vs_fp64"] = acc
     env.close()
     if rank == 0 and not args.no_cpu:
         v, desc, cores = cpu_sample(args.cpu_seconds, wl)

@@ -265,7 +265,9 @@ fpeps_status fpeps_svd_f64(const double* M, int32_t k, double* U, double* sigma,
  *   1 <= k <= FPEPS_SVD_NOALLOC_MAX_K; larger k returns FPEPS_ERR_ARG.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture. Calls share the array: calls that overlap on the GPU (other streams,
+ * capture. The address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, and the entry point must not be
+ * called on that device again. Calls share the array: calls that overlap on the GPU (other streams,
  * other host threads) race. Synchronises `cuda_stream`. */
 fpeps_status fpeps_svd_f64_noalloc(const double* M, int32_t k, double* U, double* sigma, double* V,
                                    void* cuda_stream);

@@ -68,6 +68,25 @@ def bdim(A: np.ndarray, W: np.ndarray, leg: int) -> int:
 # the four matrix applications used by the compression (pattern of Fig. 2(a))
 # ---------------------------------------------------------------------------
 
+# The four maps are linear in their k input vectors (last axis); they are applied to at most
+# COLS vectors at a time, which bounds the size of the intermediates (at 6x6, D=6, chi=256 a
+# full-width intermediate would hold ~11 GB) without changing any vector's arithmetic.
+COLS = 16
+
+
+def _by_columns(fn):
+    def wrapped(E, T, A, W, X):
+        k = X.shape[-1]
+        if k <= COLS:
+            return fn(E, T, A, W, X)
+        parts = [fn(E, T, A, W, X[..., j:j + COLS]) for j in range(0, k, COLS)]
+        return np.concatenate(parts, axis=-1)
+    wrapped.__doc__ = fn.__doc__
+    wrapped.__name__ = fn.__name__
+    return wrapped
+
+
+@_by_columns
 def theta(EL, T, A, W, X):
     """Theta_c X: X[t', R, k] -> [a, Dn, k];  Theta = EL . T . C (left environment side)."""
     G1 = np.einsum("tUs,sRk->tURk", T, X, optimize=True)
@@ -75,6 +94,7 @@ def theta(EL, T, A, W, X):
     return np.einsum("atL,tLDk->aDk", EL, G2, optimize=True)
 
 
+@_by_columns
 def theta_t(EL, T, A, W, Y):
     """Theta_c^T Y: Y[a, Dn, k] -> [t', R, k]."""
     H1 = np.einsum("atL,aDk->tLDk", EL, Y, optimize=True)
@@ -82,6 +102,7 @@ def theta_t(EL, T, A, W, Y):
     return np.einsum("tUs,tURk->sRk", T, H2, optimize=True)
 
 
+@_by_columns
 def theta_r(ER, T, A, W, X):
     """Right-environment map: X[Dn, a, k] -> [t, L, k];  ER[a, t', R] is the environment to the right."""
     W1 = np.einsum("asR,Dak->sRDk", ER, X, optimize=True)
@@ -89,6 +110,7 @@ def theta_r(ER, T, A, W, X):
     return np.einsum("tUs,sLUk->tLk", T, W2, optimize=True)
 
 
+@_by_columns
 def theta_r_t(ER, T, A, W, Z):
     """Transpose of theta_r: Z[t, L, k] -> [Dn, a, k]."""
     W1 = np.einsum("tUs,tLk->sLUk", T, Z, optimize=True)

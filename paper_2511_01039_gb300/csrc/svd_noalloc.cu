@@ -16,8 +16,11 @@
 // host-side stand-in, not device memory, so it is never handed to a kernel
 // directly: on the first call on a device (with that device current) its device
 // address is looked up once with cudaGetSymbolAddress and cached; later calls
-// on that device reuse it. All calls share the array: calls whose work overlaps
-// on the GPU (different streams, or different host threads) race on it.
+// on that device reuse it. The cached address belongs to the device's primary
+// context: after cudaDeviceReset (which destroys that context) it is stale, so a
+// process that resets a device must not call this entry point on it again. All
+// calls share the array: calls whose work overlaps on the GPU (different streams,
+// or different host threads) race on it.
 #include <exception>
 #include <mutex>
 

@@ -207,3 +207,53 @@ def test_c2_against_stored_oracle(fp, decay, prec, tol):
     assert sn == gold["num_sign"] and sd == gold["den_sign"]
     assert abs(ln - gold["num_log"]) < tol
     assert abs(ld - gold["den_log"]) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("tf32x3", 1e-5 * TF32X3_OVER_F32)])
+def test_k_column_slicing_matches_oracle(fp, monkeypatch, prec, tol):
+    """The Theta applications slice their O(chi^2 (DwD)^2) intermediates over the sketch
+    columns (chunks of FPEPS_CHUNK_ELEMS elements). A small budget forces several chunks
+    (kc < k) in every application, as the 8x8 chi=500 row does (kc = 46 of 510); the result
+    must still equal the oracle's, and in FP64 the unsliced run to rounding."""
+    peps = L.decaying_peps(4, 4, 2, 4, seed=3)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=3))
+    prm_o = B.RsvdParams(oversample=6, power_iters=2, n_fit=1)
+    sn_o, ln_o = B.contract(peps, pepo, 12, prm_o, seed=5, layer=1)
+
+    def run(budget):
+        if budget:
+            monkeypatch.setenv("FPEPS_CHUNK_ELEMS", str(budget))
+        else:
+            monkeypatch.delenv("FPEPS_CHUNK_ELEMS", raising=False)
+        env = _env(fp, peps, pepo, D=2, w=4, chi=12, prec=prec, seed=5)
+        for r in range(4):
+            fp.fpeps_absorb_row(env.h, r, 1)
+            if 0 < r < 3:
+                fp.fpeps_compress_rsvd(env.h, fp.params(6, 2, 0, 1, 0))
+        v = fp.fpeps_sweep_value(env.h)
+        env.close()
+        return v
+
+    # per vector, an application holds t * max(U R, L Dn) <= 12 * 16 * 16 = 3072 elements per
+    # intermediate here, so 3 * 3072 gives chunks of at most 3 of the 18 sketch columns
+    sg, lg = run(3 * 3072)
+    assert sg == sn_o and abs(lg - ln_o) < tol
+    s0, l0 = run(None)
+    assert s0 == sg
+    if prec == "f64":
+        assert abs(lg - l0) < 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("tf32x3", 1e-5 * TF32X3_OVER_F32)])
+def test_k_column_slicing_c2_stored_oracle(fp, monkeypatch, prec, tol):
+    """C2 (4x4, D=4, chi=64, decaying PEPS) with chunks of 4 sketch columns of 74."""
+    gold = json.load(open(os.path.join(HERE, "golden", "c2_fsm_decay_seed0.json")))
+    peps = L.decaying_peps(4, 4, 4, 4, seed=gold["peps_seed"])
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=gold["ham_seed"]))
+    # t * max(U R, L Dn) <= 64 * 64 * 64 elements per vector
+    monkeypatch.setenv("FPEPS_CHUNK_ELEMS", str(4 * 64 * 64 * 64))
+    env = _env(fp, peps, pepo, D=4, w=4, chi=64, prec=prec, seed=gold["sketch_seed"])
+    val, sn, ln = env.expect(fp.params(10, 2, 0, 1, 0))
+    env.close()
+    assert sn == gold["num_sign"]
+    assert abs(ln - gold["num_log"]) < tol

@@ -29,7 +29,9 @@ def _case(k, seed):
     return np.linalg.qr(A0)[1].T.copy()     # the path factorises R^T of a thin QR
 
 
-@pytest.mark.parametrize("k", [64, 200])   # one-block and whole-GPU Jacobi
+# one-block and whole-GPU Jacobi; 256 is the largest k the array holds (its counter area ends
+# exactly at the end of the array)
+@pytest.mark.parametrize("k", [64, 200, 256])
 def test_noalloc_svd_matches_allocating_svd_twice(fp, k):
     import torch
     for seed in (1, 2):                    # two calls in a row: the shared array is reused
