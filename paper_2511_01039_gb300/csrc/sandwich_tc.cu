@@ -22,12 +22,14 @@
 //   * D2 leaves through shared memory with coalesced stores: the output bundle of
 //     unit stride is stored PEPO-index outermost (bundle_index), so every output pair
 //     owns contiguous runs.
-// Warp roles (16 warps): 0 bulk copies, 1 tensor-memory allocation and MMA issue, 4-7
-// ket-A producers, 8-11 epilogue (two D2 accumulators, so the bra of the next pair does not
-// wait for the stores), 12-15 transposer. The MMA warp polls both streams and issues whichever
-// is ready, so the ket of the next pair overlaps the transposition of the current one. Every
-// wait is bounded; on a timeout the CTA raises its abort flag, waits (bounded) for its bulk
-// copies and MMAs, frees its tensor memory and exits.
+// Warp roles (16 warps): 0 bulk copies, 1 tensor-memory allocation and the ket MMAs, 2-3 the
+// bra MMAs (one warp per bra-A slot, each into its own half of D2), 4-7 ket-A producers, 8-11
+// epilogue (adds the D2 halves; releases D2 before its stores), 12-15 transposer. A tcgen05.mma
+// occupies its issuing thread for roughly the same ~100 cycles at any N up to ~200 (measured on
+// GB300, M = 128, kind::tf32), so the narrow bra products are issued from two threads, and the ket
+// of the next pair, issued from a third, overlaps the bra of the current one. Every wait is
+// bounded; on a timeout the CTA raises its abort flag, waits (bounded) for its bulk copies and
+// MMAs, frees its tensor memory and exits.
 #include <algorithm>
 
 #include "common.cuh"
@@ -67,7 +69,7 @@ static_assert(TM_D2 >= N1MAX && TM_D2 + TM_D2_STRIDE + N2MAX <= TM_KA && TM_KA +
                   TM_BA + 2 * 2 * KPAD <= TM_COLS, "tensor memory");
 static_assert(TM_D2 % 32 == 0 && TM_D2_STRIDE % 32 == 0 && TM_KA % 16 == 0 && TM_BA % 16 == 0 && (2 * KPAD) % 16 == 0,
               "alignment");
-constexpr int W_BULK = 0, W_MMA = 1, W_KA0 = 4, W_EP0 = 8, W_TR0 = 12;
+constexpr int W_BULK = 0, W_MMA = 1, W_BRA0 = 2, W_KA0 = 4, W_EP0 = 8, W_TR0 = 12;
 
 struct SwArgs {
   int nx, ny, nv, nz, p, nxw, nyw, nvw, nzw, npair;
@@ -163,6 +165,15 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
 }
 
+// every MMA issued by this thread has completed (bounded wait; the drain barrier counts one
+// commit per issuing thread) before the tensor memory is freed
+__device__ __forceinline__ void drain_mmas(uint64_t* drain) {
+  mma_commit<false>(drain);
+  const unsigned long long t0 = clock64();
+  while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
+  }
+}
+
 __global__ void __launch_bounds__(SW_THREADS, 1) k_sandwich_tc(const SwArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* bars = (uint64_t*)(smem + OFF_BAR);
@@ -174,9 +185,9 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_sandwich_tc(const SwArgs a) {
   uint64_t* ba_empty = ba_full + 2;
   uint64_t* d1_full = ba_empty + 2;           // ket accumulator complete / read
   uint64_t* d1_empty = d1_full + 1;
-  uint64_t* d2_full = d1_empty + 1;           // [2] bra accumulators complete / read
-  uint64_t* d2_empty = d2_full + 2;
-  uint64_t* ar_full = d2_empty + 2;
+  uint64_t* d2_full = d1_empty + 1;           // both bra accumulator halves complete / read
+  uint64_t* d2_empty = d2_full + 1;
+  uint64_t* ar_full = d2_empty + 1;
   uint64_t* drain = ar_full + 1;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -196,13 +207,13 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_sandwich_tc(const SwArgs a) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(&ba_full[s], 4);
       mbar_init(&ba_empty[s], 1);
-      mbar_init(&d2_full[s], 1);
-      mbar_init(&d2_empty[s], 4);
     }
+    mbar_init(d2_full, 2);
+    mbar_init(d2_empty, 4);
     mbar_init(d1_full, 1);
     mbar_init(d1_empty, 4);
     mbar_init(ar_full, 1);
-    mbar_init(drain, 1);
+    mbar_init(drain, 3);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -251,92 +262,87 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_sandwich_tc(const SwArgs a) {
       }
     }
   } else if (warp == W_MMA) {
-    // Two MMA streams, issued as their inputs become ready (non-blocking polls): the ket of pair
-    // k into D1 and the bra of pair b < k into D2[b % 2]. The ket of pair k needs D1 read by the
-    // transposer (pair k - 1); the bra of pair b needs D2[b % 2] drained by the epilogue (pair b - 2).
+    // ket MMAs: the channels of pair k into D1, once the transposer has read pair k - 1
     if (lane == 0) {
       const uint32_t idesc1 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.n1p >> 3) << 17) | ((128u >> 4) << 24);
-      const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.n2p >> 3) << 17) | ((128u >> 4) << 24);
-      const uint32_t lbo1 = (uint32_t)(a.n1p / 8) * 128, lbo2 = (uint32_t)(a.n2p / 8) * 128;
-      const int nkk1 = KPAD / 8, nkk2 = a.k2p / 8;
-      bool ok = mbar_wait(ar_full, 0, abort_flag);
-      PairIter kp, bp;
+      const uint32_t lbo1 = (uint32_t)(a.n1p / 8) * 128;
+      PairIter kp;
       kp.start(s_poff);
-      bp.start(s_poff);
-      bool k_have = ok && kp.next(a), b_have = ok && bp.next(a);
-      int k = 0, kc = 0, it = 0;   // ket: pair count, channel in the pair, channels issued
-      int b = 0, bq = 0, qi = 0;   // bra: pair count, q in the pair, q steps issued
-      bool k_go = true, b_go = false;   // the pair's D1 / D2 buffer is free
-      unsigned long long t_last = clock64();
-      while (ok && (k_have || b_have)) {
-        bool progress = false;
-        if (b_have && b < k) {
-          if (!b_go && bq == 0) b_go = mbar_test_wait(&d2_empty[b & 1], ((b >> 1) & 1) ^ 1);
-          if (b_go && mbar_test_wait(&ba_full[qi & 1], (qi >> 1) & 1)) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint8_t* bh = smem + OFF_AR + bq * 2 * ar_bytes;
-            const uint8_t* bl = bh + ar_bytes;
-            const uint32_t ah = tmem + TM_BA + (qi & 1) * 2 * KPAD, al = ah + KPAD;
-            const uint32_t d = tmem + TM_D2 + (b & 1) * TM_D2_STRIDE;
-            for (int kk = 0; kk < nkk2; ++kk) {
-              const uint32_t acc = (bq > 0 || kk > 0) ? 1u : 0u;
-              mma_ts(d, al + kk * 8, sdesc_noswz(bh + 2 * kk * lbo2, lbo2, 128), idesc2, acc);
-              mma_ts(d, ah + kk * 8, sdesc_noswz(bl + 2 * kk * lbo2, lbo2, 128), idesc2, 1u);
-              mma_ts(d, ah + kk * 8, sdesc_noswz(bh + 2 * kk * lbo2, lbo2, 128), idesc2, 1u);
-            }
-            mma_commit<false>(&ba_empty[qi & 1]);
-            ++qi;
-            if (++bq == P) {
-              mma_commit<false>(&d2_full[b & 1]);
-              ++b;
-              bq = 0;
-              b_go = false;
-              b_have = bp.next(a);
-            }
-            progress = true;
-          }
-        }
-        if (k_have) {
-          if (!k_go && kc == 0) k_go = mbar_test_wait(d1_empty, (k - 1) & 1);
+      int k = 0, it = 0;
+      bool ok = true;
+      while (ok && kp.next(a)) {
+        if (k > 0 && !mbar_wait(d1_empty, (k - 1) & 1, abort_flag)) break;
+        for (int c = kp.c0(); c < kp.c1(); ++c, ++it) {
           const int st = it % KB_STAGES;
-          if (k_go && mbar_test_wait(&kb_full[st], (it / KB_STAGES) & 1) && mbar_test_wait(ka_full, it & 1)) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint8_t* bh = smem + OFF_KB + st * 2 * KB_IMG;
-            const uint8_t* bl = bh + kb_bytes;
-            const uint32_t ah = tmem + TM_KA, al = ah + KPAD;
-            for (int kk = 0; kk < nkk1; ++kk) {
-              const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-              mma_ts(tmem + TM_D1, al + kk * 8, sdesc_noswz(bh + 2 * kk * lbo1, lbo1, 128), idesc1, acc);
-              mma_ts(tmem + TM_D1, ah + kk * 8, sdesc_noswz(bl + 2 * kk * lbo1, lbo1, 128), idesc1, 1u);
-              mma_ts(tmem + TM_D1, ah + kk * 8, sdesc_noswz(bh + 2 * kk * lbo1, lbo1, 128), idesc1, 1u);
-            }
-            mma_commit<false>(&kb_empty[st]);
-            mma_commit<false>(ka_empty);
-            ++it;
-            if (++kc == kp.c1() - kp.c0()) {
-              mma_commit<false>(d1_full);
-              ++k;
-              kc = 0;
-              k_go = false;
-              k_have = kp.next(a);
-            }
-            progress = true;
+          if (!mbar_wait(&kb_full[st], (it / KB_STAGES) & 1, abort_flag) || !mbar_wait(ka_full, it & 1, abort_flag)) {
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* bh = smem + OFF_KB + st * 2 * KB_IMG;
+          const uint8_t* bl = bh + kb_bytes;
+          const uint32_t ah = tmem + TM_KA, al = ah + KPAD;
+#pragma unroll
+          for (int kk = 0; kk < KPAD / 8; ++kk) {
+            const uint32_t acc = (c > kp.c0() || kk > 0) ? 1u : 0u;
+            mma_ts(tmem + TM_D1, al + kk * 8, sdesc_noswz(bh + 2 * kk * lbo1, lbo1, 128), idesc1, acc);
+            mma_ts(tmem + TM_D1, ah + kk * 8, sdesc_noswz(bl + 2 * kk * lbo1, lbo1, 128), idesc1, 1u);
+            mma_ts(tmem + TM_D1, ah + kk * 8, sdesc_noswz(bh + 2 * kk * lbo1, lbo1, 128), idesc1, 1u);
+          }
+          mma_commit<false>(&kb_empty[st]);
+          mma_commit<false>(ka_empty);
         }
-        if (progress) {
-          t_last = clock64();
-        } else if (*abort_flag) {
-          ok = false;
-        } else if (clock64() - t_last > WAIT_LIMIT) {
-          *abort_flag = 1;
-          ok = false;
+        if (!ok) break;
+        mma_commit<false>(d1_full);
+        ++k;
+      }
+      drain_mmas(drain);
+    }
+    __syncwarp();
+  } else if (warp == W_BRA0 || warp == W_BRA0 + 1) {
+    // bra MMAs: warp W_BRA0 + w takes the q blocks that arrive in bra-A slot w (the transposer
+    // fills the two slots alternately, so both warps get q blocks of every pair when p >= 2) and
+    // accumulates them into D2 half w; the epilogue adds the halves. A tcgen05.mma costs its
+    // issuing thread about the same time for any N up to ~200, so two issuers run the narrow
+    // (N = 48) bra products at twice the rate of one.
+    if (lane == 0) {
+      const int w = warp - W_BRA0;
+      const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.n2p >> 3) << 17) | ((128u >> 4) << 24);
+      const uint32_t lbo2 = (uint32_t)(a.n2p / 8) * 128;
+      const int nkk2 = a.k2p / 8;
+      const uint32_t ah = tmem + TM_BA + w * 2 * KPAD, al = ah + KPAD;
+      const uint32_t d = tmem + TM_D2 + w * TM_D2_STRIDE;
+      bool ok = mbar_wait(ar_full, 0, abort_flag);
+      PairIter bp;
+      bp.start(s_poff);
+      int b = 0;
+      while (ok && bp.next(a)) {
+        if (b > 0 && !mbar_wait(d2_empty, (b - 1) & 1, abort_flag)) break;
+        bool first = true;
+        for (int q = 0; q < P; ++q) {
+          const int qi = P * b + q;   // q blocks run through the two slots in this order
+          if ((qi & 1) != w) continue;
+          if (!mbar_wait(&ba_full[w], (qi >> 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* bh = smem + OFF_AR + q * 2 * ar_bytes;
+          const uint8_t* bl = bh + ar_bytes;
+          for (int kk = 0; kk < nkk2; ++kk) {
+            const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+            mma_ts(d, al + kk * 8, sdesc_noswz(bh + 2 * kk * lbo2, lbo2, 128), idesc2, acc);
+            mma_ts(d, ah + kk * 8, sdesc_noswz(bl + 2 * kk * lbo2, lbo2, 128), idesc2, 1u);
+            mma_ts(d, ah + kk * 8, sdesc_noswz(bh + 2 * kk * lbo2, lbo2, 128), idesc2, 1u);
+          }
+          mma_commit<false>(&ba_empty[w]);
+          first = false;
         }
+        if (!ok) break;
+        mma_commit<false>(d2_full);
+        ++b;
       }
-      // every MMA issued by this thread has completed before the tensor memory is freed
-      mma_commit<false>(drain);
-      const unsigned long long t0 = clock64();
-      while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT) {
-      }
+      drain_mmas(drain);
     }
     __syncwarp();
   } else if (warp >= W_KA0 && warp < W_EP0) {
@@ -448,26 +454,39 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_sandwich_tc(const SwArgs a) {
           }
         continue;
       }
-      uint32_t r2[RMAX];
-      bool okw = warp_wait(&d2_full[pn & 1], (pn >> 1) & 1, abort_flag);
+      bool okw = warp_wait(d2_full, pn & 1, abort_flag);
       if (okw) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        {
-          const uint32_t t2 = tmem + lane_base + TM_D2 + (pn & 1) * TM_D2_STRIDE;
+        float4* srow = (float4*)(estg + row * RMAX);
+        // the two halves of D2 (the q blocks of bra slot 0 and of slot 1) are added here; each half
+        // is read in turn to keep the registers of one half live
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t r2[RMAX];
+          const uint32_t t2 = tmem + lane_base + TM_D2 + hh * TM_D2_STRIDE;
           if (R2 > 4) tmem_ld32_async(t2, r2);
           else tmem_ld4(t2, r2);
           if (R2 > 32) tmem_ld4(t2 + 32, r2 + 32);
-        }
-        tmem_wait_tie(r2);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&d2_empty[pn & 1]);
-        float4* srow = (float4*)(estg + row * RMAX);
+          tmem_wait_tie(r2);
+          if (hh == 1) {
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(d2_empty);
+          }
 #pragma unroll
-        for (int j = 0; j < RMAX / 4; ++j)
-          if (j * 4 < R2)
-            srow[j] = make_float4(__uint_as_float(r2[4 * j]), __uint_as_float(r2[4 * j + 1]),
-                                  __uint_as_float(r2[4 * j + 2]), __uint_as_float(r2[4 * j + 3]));
+          for (int j = 0; j < RMAX / 4; ++j)
+            if (j * 4 < R2) {
+              float4 v = make_float4(__uint_as_float(r2[4 * j]), __uint_as_float(r2[4 * j + 1]),
+                                     __uint_as_float(r2[4 * j + 2]), __uint_as_float(r2[4 * j + 3]));
+              if (hh == 1) {
+                const float4 u = srow[j];
+                v.x += u.x;
+                v.y += u.y;
+                v.z += u.z;
+                v.w += u.w;
+              }
+              srow[j] = v;
+            }
+        }
       }
       if (!named_sync_and(3, 128, okw)) { ok = false; break; }
       for (int bb = 0; bb < nbv; ++bb)
@@ -655,7 +674,7 @@ TcShape tc_shape(const SandOrient& o) {
 
 bool sandwich_tc_fits(const SandOrient& o) {
   const TcShape t = tc_shape(o);
-  return o.nch >= 1 && o.nch <= CHMAX && o.nvw * o.nzw <= PAIRMAX && o.p >= 1 && o.p <= PMAX && o.nx >= 1 && o.ny >= 1 && o.nv >= 1 && o.nz >= 1 && o.nx <= 6 &&
+  return o.nch >= 1 && o.nch <= CHMAX && o.nvw * o.nzw <= PAIRMAX && o.p >= 2 && o.p <= PMAX && o.nx >= 1 && o.ny >= 1 && o.nv >= 1 && o.nz >= 1 && o.nx <= 6 &&
          o.ny <= 6 && o.nv <= 6 && o.nz <= 6 && t.r1 <= RMAX && t.r2 <= RMAX && t.n1p <= N1MAX && t.k2p <= KPAD &&
          t.n2p <= N2MAX;
 }
