@@ -661,6 +661,17 @@ struct Engine : EngineBase {
     }
   }
 
+  // A basis of col(Y) for the next step of the subspace iteration: one CholeskyQR pass,
+  // Y R1^-1. Its columns are orthonormal only to O(cond(Y)^2 u), but it equals the two-pass Q
+  // times an upper-triangular matrix with a positive diagonal (R2), and Gram-Schmidt in
+  // column order is invariant under such a factor: every later orthonormalisation, and so
+  // the final Q, is the same as with two passes here, up to rounding.
+  void qr_basis(const T* Y, int64_t m, int k, T* Q) {
+    Phase ph_(this, 1);
+    Arena ar = arena();
+    one_pass(ar, Y, m, k, Q, nullptr, PASS_PLAIN);
+  }
+
   // ---------------------------------------------------------------- rSVD (Sec. IV)
   struct Lin {
     int64_t m, n;
@@ -676,7 +687,8 @@ struct Engine : EngineBase {
     std::vector<double> sigma;
   };
   // Randomized subspace iteration with re-orthonormalisation after every
-  // application, then B = Q^T A = R_b^T Q_b^T and the Jacobi SVD of R_b^T.
+  // application (one CholeskyQR pass for the intermediate bases, two for the last),
+  // then B = Q^T A = R_b^T Q_b^T and the Jacobi SVD of R_b^T.
   RsvdOut rsvd(Arena& ar, Lin& A, const T* omega, int k, int q) {
     RsvdOut r;
     const int64_t m = A.m, n = A.n;
@@ -684,13 +696,16 @@ struct Engine : EngineBase {
     T* Z = ar.get_n<T>(n * k);
     r.Q = ar.get_n<T>(m * k);
     T* Qz = ar.get_n<T>(n * k);
+    // intermediate bases of the iteration take one CholeskyQR pass (qr_basis), the last Q two
     A.fwd(omega, Y, k);
-    qr(Y, m, k, r.Q, nullptr);
+    if (q > 0) qr_basis(Y, m, k, r.Q);
+    else qr(Y, m, k, r.Q, nullptr);
     for (int it = 0; it < q; ++it) {
       A.bwd(r.Q, Z, k);
-      qr(Z, n, k, Qz, nullptr);
+      qr_basis(Z, n, k, Qz);
       A.fwd(Qz, Y, k);
-      qr(Y, m, k, r.Q, nullptr);
+      if (it + 1 < q) qr_basis(Y, m, k, r.Q);
+      else qr(Y, m, k, r.Q, nullptr);
     }
     (A.bwd_last ? A.bwd_last : A.bwd)(r.Q, Z, k);   // B^T = A^T Q  (n x k)
     double* Rb = ar.get_n<double>((int64_t)k * k);

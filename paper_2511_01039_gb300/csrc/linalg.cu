@@ -399,108 +399,163 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(double* M, double* V, int k
   if (threadIdx.x == 0) info[0] = 0;
 }
 
-// The same method spread over the whole GPU: one warp per column pair, a grid
-// barrier (cooperative launch) between rounds. ws[0..3]: sweep rotation
-// counters (two, alternating) and the squared Frobenius norm.
-// One rotation of the pair (p, q) by one warp: both columns of M and of V are
-// loaded into registers at once (NI elements per lane), so a round costs one
-// memory latency instead of one per 32 elements. Returns true if it rotated.
-template <int NI>
-__device__ __forceinline__ bool jacobi_rotate_pair(double* __restrict__ mp, double* __restrict__ mq,
-                                                   double* __restrict__ vp, double* __restrict__ vq, int k, int lane,
-                                                   double eps, double tiny) {
-  double x[NI], y[NI], a[NI], b[NI];
-#pragma unroll
-  for (int t = 0; t < NI; ++t) {
-    const int i = lane + 32 * t;
-    const bool in = i < k;
-    x[t] = in ? mp[i] : 0.0;
-    y[t] = in ? mq[i] : 0.0;
-    a[t] = in ? vp[i] : 0.0;
-    b[t] = in ? vq[i] : 0.0;
-  }
+// The same method spread over the whole GPU, in blocks of two columns (block b:
+// columns 2b and 2b + 1). A round-robin schedule over the blocks gives every CTA a
+// pair of blocks (A, B) per round; the CTA copies their four columns of M and of V to
+// shared memory and rotates the four cross pairs, two at a time ((a0,b0) (a1,b1), then
+// (a0,b1) (a1,b0)), after first rotating each block's own pair in the first round of a
+// sweep. Every column pair is visited once per sweep, as in the scalar cyclic order,
+// with one grid barrier per round of blocks. Each rotation is carried by two warps (one
+// half of the rows each, partial dot products exchanged in shared memory), so the four
+// warps of a CTA keep all four FP64 pipes of the SM busy: FP64 is the limit here (~2 FMA
+// per cycle per SM on this part; a rotation of two length-k columns of M and of V costs
+// ~11 k FMA).
+// ws[0..1]: sweep rotation counters (two, alternating), ws[2]: squared Frobenius norm,
+// ws[3]: sweeps used, ws[4..5]: counters of rotations above sqrt(big2) (alternating).
+constexpr int JB_THREADS = 128;
+
+// rotation of local columns (p, q) by the two warps h = 0, 1 of a pair slot: rows
+// [h * half, (h + 1) * half); part[6] holds the two halves' (alpha, beta, gamma)
+// *big (if given) is set when the rotation's |gamma| / sqrt(alpha beta) exceeds sqrt(big2)
+__device__ __forceinline__ bool jacobi_rotate_split(double* __restrict__ mp, double* __restrict__ mq,
+                                                    double* __restrict__ vp, double* __restrict__ vq, int k, int h,
+                                                    int lane, double* part, double eps, double tiny, bool* big,
+                                                    double big2) {
+  const int half = (k + 1) / 2, i0 = h * half, i1 = min(k, i0 + half);
   double al = 0, be = 0, ga = 0;
-#pragma unroll
-  for (int t = 0; t < NI; ++t) {
-    al = fma(x[t], x[t], al);
-    be = fma(y[t], y[t], be);
-    ga = fma(x[t], y[t], ga);
+  for (int i = i0 + lane; i < i1; i += 32) {
+    const double x = mp[i], y = mq[i];
+    al = fma(x, x, al);
+    be = fma(y, y, be);
+    ga = fma(x, y, ga);
   }
   for (int o = 16; o; o >>= 1) {
     al += __shfl_xor_sync(0xffffffffu, al, o);
     be += __shfl_xor_sync(0xffffffffu, be, o);
     ga += __shfl_xor_sync(0xffffffffu, ga, o);
   }
-  if (ga == 0.0 || fmin(al, be) <= tiny || fabs(ga) <= eps * sqrt(al) * sqrt(be)) return false;
-  const double zeta = (be - al) / (2.0 * ga);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-#pragma unroll
-  for (int u = 0; u < NI; ++u) {
-    const int i = lane + 32 * u;
-    if (i < k) {
-      mp[i] = c * x[u] - sn * y[u];
-      mq[i] = sn * x[u] + c * y[u];
-      vp[i] = c * a[u] - sn * b[u];
-      vq[i] = sn * a[u] + c * b[u];
+  if (lane == 0) {
+    part[3 * h + 0] = al;
+    part[3 * h + 1] = be;
+    part[3 * h + 2] = ga;
+  }
+  __syncthreads();
+  // both warps add the halves in the same order, so they take the same decision and angle
+  al = part[0] + part[3];
+  be = part[1] + part[4];
+  ga = part[2] + part[5];
+  // |gamma| <= eps sqrt(alpha beta) tested squared: FP64 sqrt and division are long serial
+  // latencies here (~680 and ~430 cycles), so the angle takes one of each plus one rsqrt:
+  // tan = sign(d) 2 gamma / (|d| + sqrt(d^2 + 4 gamma^2)), d = beta - alpha, which is
+  // sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = d / (2 gamma)
+  const bool rot = !(ga == 0.0 || fmin(al, be) <= tiny || ga * ga <= eps * eps * al * be);
+  if (rot) {
+    if (big && ga * ga > big2 * al * be) *big = true;
+    const double d = be - al, g2 = 2.0 * ga;
+    const double t = (d >= 0 ? g2 : -g2) / (fabs(d) + sqrt(fma(d, d, g2 * g2)));
+    const double c = rsqrt(fma(t, t, 1.0)), sn = c * t;
+    for (int i = i0 + lane; i < i1; i += 32) {
+      const double x = mp[i], y = mq[i], a = vp[i], b = vq[i];
+      mp[i] = c * x - sn * y;
+      mq[i] = sn * x + c * y;
+      vp[i] = c * a - sn * b;
+      vq[i] = sn * a + c * b;
     }
   }
-  return true;
+  return rot;
 }
 
-// Cooperative one-sided Jacobi over the whole GPU: round-robin pair schedule,
-// one warp per pair, a grid barrier between rounds. NI * 32 >= k.
-template <int NI>
-__global__ void __launch_bounds__(256) k_jacobi_svd_coop(double* M, double* V, int k, int max_sweeps, double eps,
-                                                         unsigned long long* ws) {
+__global__ void __launch_bounds__(JB_THREADS) k_jacobi_svd_blk(double* M, double* V, int k, int max_sweeps,
+                                                                double eps, double big2, unsigned long long* ws) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  const int kk = (k % 2) ? k + 1 : k;
-  const int lane = threadIdx.x % 32;
-  const int gwarp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int nwarps = gridDim.x * (blockDim.x / 32);
+  extern __shared__ double jsh[];   // M columns [4][k], V columns [4][k], partial dots [2][6]
+  double* sm = jsh;
+  double* sv = jsh + 4 * (int64_t)k;
+  double* part = jsh + 8 * (int64_t)k;
+  const int nb = (k + 1) / 2, nbe = nb + (nb & 1);   // blocks; a dummy block when nb is odd
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int slot = warp / 2, h = warp % 2;           // pair slot and row half of this warp
   double* fro2p = (double*)&ws[2];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k; e += (int64_t)gridDim.x * blockDim.x)
     V[e] = ((e / k) == (e % k)) ? 1.0 : 0.0;
   if (blockIdx.x == 0) {   // ||M||_F^2 by block 0
-    __shared__ double red[32];
+    __shared__ double red[JB_THREADS / 32];
     double f = 0;
     for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) f = fma(M[e], M[e], f);
     for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0) red[threadIdx.x / 32] = f;
+    if (lane == 0) red[warp] = f;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+      for (int w = 0; w < JB_THREADS / 32; ++w) t += red[w];
       *fro2p = t;
-      ws[0] = 0;
-      ws[1] = 0;
+      ws[0] = ws[1] = ws[4] = ws[5] = 0;
     }
   }
   grid.sync();
   const double tiny = 1e-30 * (*fro2p);
-  // The rotation counter of sweep s lives in ws[s & 1] (nobody else touches it
-  // during sweep s). After the last round every block reads it and a further
-  // barrier follows, so all blocks take the same break decision; the slot is
-  // cleared for sweep s+2 at round 1 of sweep s+1, after those reads.
+  // The rotation counter of sweep s lives in ws[s & 1] (its count of rotations above
+  // sqrt(big2) in ws[4 + (s & 1)]); every block reads it after the last
+  // round and a further barrier follows, so all blocks take the same break decision; the slot
+  // is cleared for sweep s+2 at round 1 of sweep s+1, after those reads.
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int round = 0; round < kk - 1; ++round) {
-      if (round == 1 && blockIdx.x == 0 && threadIdx.x == 0) ws[(sweep + 1) & 1] = 0;
-      for (int pr = gwarp; pr < kk / 2; pr += nwarps) {
-        int a = rr_player(pr, round, kk), b = rr_player(kk - 1 - pr, round, kk);
-        int p = min(a, b), q = max(a, b);
-        if (q >= k) continue;
-        if (jacobi_rotate_pair<NI>(M + (int64_t)p * k, M + (int64_t)q * k, V + (int64_t)p * k, V + (int64_t)q * k, k,
-                                   lane, eps, tiny) &&
-            lane == 0)
-          atomicAdd(&ws[sweep & 1], 1ull);
+    for (int round = 0; round < nbe - 1; ++round) {
+      if (round == 1 && blockIdx.x == 0 && threadIdx.x == 0) ws[(sweep + 1) & 1] = ws[4 + ((sweep + 1) & 1)] = 0;
+      const int A = rr_player((int)blockIdx.x, round, nbe), B = rr_player(nbe - 1 - (int)blockIdx.x, round, nbe);
+      // local columns 0, 1 (block A) and 2, 3 (block B); -1: absent
+      int col[4];
+      col[0] = 2 * A;
+      col[1] = 2 * A + 1;
+      col[2] = 2 * B;
+      col[3] = 2 * B + 1;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (col[j] >= k) col[j] = -1;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+          const bool in = col[j] >= 0;
+          sm[j * k + i] = in ? M[(int64_t)col[j] * k + i] : 0.0;
+          sv[j * k + i] = in ? V[(int64_t)col[j] * k + i] : 0.0;
+        }
+      __syncthreads();
+      int nrot = 0;
+      bool big = false;
+      // inner rounds: the blocks' own pairs (first round of a sweep), then the cross pairs
+      // inner round 0: (0,1) (2,3); 1: (0,2) (1,3); 2: (0,3) (1,2) -- slot 0 takes the first pair
+      for (int ir = round == 0 ? 0 : 1; ir < 3; ++ir) {
+        const int p = ir == 0 ? 2 * slot : slot;
+        const int q = ir == 0 ? 2 * slot + 1 : (ir == 1 ? slot + 2 : 3 - slot);
+        double* pt = part + 6 * slot;
+        if (col[p] >= 0 && col[q] >= 0) {
+          if (jacobi_rotate_split(sm + p * k, sm + q * k, sv + p * k, sv + q * k, k, h, lane, pt, eps, tiny, &big,
+                                  big2))
+            ++nrot;
+        } else {
+          __syncthreads();   // the same barrier count as a rotating slot
+        }
+        __syncthreads();
       }
+      if (h == 0 && lane == 0 && nrot) atomicAdd(&ws[sweep & 1], (unsigned long long)nrot);
+      if (h == 0 && lane == 0 && big) atomicAdd(&ws[4 + (sweep & 1)], 1ull);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (col[j] >= 0)
+          for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            M[(int64_t)col[j] * k + i] = sm[j * k + i];
+            V[(int64_t)col[j] * k + i] = sv[j * k + i];
+          }
       grid.sync();
     }
     const unsigned long long rot = *(volatile unsigned long long*)&ws[sweep & 1];
+    const unsigned long long nbig = *(volatile unsigned long long*)&ws[4 + (sweep & 1)];
     grid.sync();
     if (blockIdx.x == 0 && threadIdx.x == 0) ws[3] = (unsigned long long)(sweep + 1);
-    if (rot == 0) break;
+    // converged: no rotation, or only rotations below sqrt(big2) relative, after which the
+    // off-diagonal products are O(big2) = O(eps / k) (quadratic convergence), so the next
+    // sweep would find nothing above eps
+    if (rot == 0 || nbig == 0) break;
   }
 }
 
@@ -837,30 +892,32 @@ void svd_jacobi_f64(cudaStream_t s, double* Mat, int k, double* U, double* sigma
     k_jacobi_svd<<<1, 1024, 0, s>>>(Mat, V, k, 30, 1e-15 * sqrt((double)k), info);
     FP_LAUNCH();
   } else {
-    // registers per lane: NI = ceil(k / 32) elements of each of the four columns
-    void* fn = k <= 256 ? (void*)k_jacobi_svd_coop<8>
-                        : k <= 576 ? (void*)k_jacobi_svd_coop<18> : (void*)k_jacobi_svd_coop<32>;
-    const int ti = k <= 256 ? 0 : (k <= 576 ? 1 : 2);
-    static int max_blocks[3] = {-1, -1, -1};
-    if (max_blocks[ti] < 0) {
+    // one CTA per pair of two-column blocks, all co-resident (cooperative launch)
+    const int nb = (k + 1) / 2, blocks = (nb + (nb & 1)) / 2;
+    const size_t smem = (8 * (size_t)k + 12) * sizeof(double);
+    static bool attr = false;
+    static int max_blocks = -1;
+    if (!attr) {
+      FP_CUDA(cudaFuncSetAttribute(k_jacobi_svd_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((8 * 1024 + 12) * sizeof(double))));
       int dev = 0, sms = 0, per = 0;
       FP_CUDA(cudaGetDevice(&dev));
       FP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 64, 0));
-      max_blocks[ti] = sms * std::max(per, 0);
+      FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_svd_blk, JB_THREADS,
+                                                            (8 * 1024 + 12) * sizeof(double)));
+      max_blocks = sms * std::max(per, 0);
+      attr = true;
     }
-    int pairs = (k + 1) / 2;
-    // FP64 runs at ~4 flop/cycle per SM here, so a rotation (~12k flop) is compute-
-    // bound on one SM: two warps per block spread the pairs of a round over the SMs
-    int blocks = std::min(max_blocks[ti], (pairs + 1) / 2);
-    FP_CHECK(blocks >= 1, FPEPS_ERR_CUDA, "svd: no co-resident blocks");
+    FP_CHECK(blocks <= max_blocks, FPEPS_ERR_CUDA, "svd: too few co-resident blocks");
+    void* fn = (void*)k_jacobi_svd_blk;
     unsigned long long* ws = (unsigned long long*)ws_dev;
     int max_sweeps = 30;
     double eps = 1e-15 * sqrt((double)k);
-    void* args[] = {&Mat, &V, &k, &max_sweeps, &eps, &ws};
+    double big2 = eps / k;
+    void* args[] = {&Mat, &V, &k, &max_sweeps, &eps, &big2, &ws};
     ProfToken pt = prof_begin(PROF_FACTOR, s, 0.0, 16.0 * k * k);
     count_launch();
-    FP_CUDA(cudaLaunchCooperativeKernel(fn, blocks, 64, args, 0, s));
+    FP_CUDA(cudaLaunchCooperativeKernel(fn, blocks, JB_THREADS, args, smem, s));
     prof_end(pt, s);
     FP_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
     static const bool trace = getenv("FPEPS_TRACE_SVD") != nullptr;   // diagnostics: sweeps used

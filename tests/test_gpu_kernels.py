@@ -55,9 +55,11 @@ def test_gemm_tc_rejects_unsupported_shapes(fp):
         assert ei.value.status == 7
 
 
-@pytest.mark.parametrize("k", [7, 64, 200, 511])
+@pytest.mark.parametrize("k", [7, 64, 97, 200, 511, 1024])
 def test_svd_f64_against_lapack(fp, k):
-    """One-sided Jacobi (single block for k <= 96, whole-GPU cooperative above) vs numpy's SVD."""
+    """One-sided Jacobi (single block for k <= 96; above, whole-GPU cooperative over blocks of
+    two columns, with a dummy block for odd block counts (k = 97) and a one-column block for
+    odd k) vs numpy's SVD."""
     import numpy as np
     import torch
     g = np.random.default_rng(k)
