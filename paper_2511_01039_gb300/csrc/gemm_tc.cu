@@ -9,8 +9,9 @@
 // x = hi + lo, both rounded to TF32 (|x - hi - lo| <= 2^-22 |x|), and the
 // product is a_lo b_hi + a_hi b_lo + a_hi b_hi (kind::tf32 MMAs, "3xTF32").
 //
-// The kernel is persistent (one CTA per SM walks a static tile schedule of
-// 128x128 output tiles, optionally split over K). A's hi/lo tiles live in tensor
+// The kernel is persistent (one CTA per SM, or one CTA pair per two SMs, walks a
+// static tile schedule of 128x128, respectively 256x192, output tiles, optionally
+// split over K). A's hi/lo tiles live in tensor
 // memory: converter warps read one 128-byte row of the landed fp32 tile per
 // thread and store hi and lo with tcgen05.st, so the MMAs take A from TMEM and
 // only B's hi/lo tiles from shared memory.
@@ -19,10 +20,10 @@
 // moves ~144 KB through it (TMA fills, the B split, the A rows, and 3 x 16 KB of B
 // read by the MMAs), ~1150 cycles at 128 B/clock against 768 cycles of MMAs. When
 // M spans more than one tile, CTA pairs (clusters of two, tcgen05 cta_group::2)
-// compute 256x128 tiles instead: each CTA holds 128 rows of A in its TMEM and 64
-// of the tile's 128 B rows in its shared memory, and rank 0 issues M=256 MMAs that
-// read B from both. B's loads, split and MMA reads per SM halve (~88 KB per
-// k-block). Converters and epilogue warps of both CTAs arrive on rank 0's
+// compute 256x192 tiles instead: each CTA holds 128 rows of A in its TMEM and 96
+// of the tile's 192 B rows in its shared memory, and rank 0 issues M=256, N=192
+// MMAs that read B from both. Per output column, B's loads, split and MMA reads
+// per SM halve. Converters and epilogue warps of both CTAs arrive on rank 0's
 // barriers; MMA completion is signalled to both CTAs by a multicast commit. Each
 // pair CTA has two sets of A converters taking alternate k-blocks.
 //
@@ -77,25 +78,40 @@ struct TcArgs {
 // 128-byte row of the landed fp32 tile each (one thread per TMEM lane), split it
 // and store hi and lo straight into a TMEM slot with tcgen05.st; only B's hi/lo
 // tiles stay in shared memory, so the MMAs read B alone from shared memory and the
-// A split costs no shared-memory writes. TMEM columns: [0,128) a chunk
-// accumulator; [128,256) a second one when every tile is a single chunk or the
-// CTA is part of a pair (chunks alternate, so the next chunk's MMAs overlap the
-// drain), else the running FP32 sum; [256,512) four A slots of 32 hi + 32 lo
-// columns, one per stage. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane
+// A split costs no shared-memory writes. TMEM columns of a single CTA: [0,128) a
+// chunk accumulator; [128,256) a second one when every tile is a single chunk
+// (chunks alternate, so the next chunk's MMAs overlap the drain), else the running
+// FP32 sum; [256,512) four A slots of 32 hi + 32 lo columns, one per stage. A pair
+// CTA: below. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane
 // quarter = warp % 4), 6..7 and 12..15 B converters (in a pair CTA 12..15 are a
 // second set of A converters), 8..11 epilogue, 16 barrier waiter for the MMA warp.
 constexpr int P_THREADS = 544;
-constexpr int T_STAGES = 4;
+// Pair tiles are 256 x 192 (N = 192 per MMA): a tcgen05.mma costs its issuing thread a
+// fixed ~58 ns (~120 SM cycles at 2.07 GHz, measured on GB300, M = 128 per SM, kind::tf32)
+// for any N up to ~200, while an N = 128 pair MMA gives each SM only ~70 cycles of tensor
+// work; N = 192 does 1.5x the work per MMA at the same cost. TMEM of a pair CTA: two
+// 192-column accumulators [0,384) and two A slots [384,512) (an A-slot ring of its own,
+// freed by the MMAs of the k-block two back); shared memory: three 40 KB stages and the
+// running sum, which also stages the final output tile (no separate epilogue tiles).
+template <bool PAIR> __host__ __device__ constexpr int t_bn() { return PAIR ? 192 : BN; }   // output columns per tile
+template <bool PAIR> __host__ __device__ constexpr int t_stages() { return PAIR ? 3 : 4; }
+template <bool PAIR> __host__ __device__ constexpr int t_aslots() { return PAIR ? 2 : 4; }
+template <bool PAIR> __host__ __device__ constexpr uint32_t t_aslot_base() { return PAIR ? 2 * 192 : 2 * BN; }
 // Shared memory: the stage ring (A fp32 | B hi (in place) | B lo; a pair CTA holds
-// half of B, so its stages are 32 KB instead of 48), then in a pair CTA the
-// running FP32 sum of multi-chunk tiles (128 rows x 129 floats, padded so that a
-// row per lane is conflict-free), the barriers, and the epilogue's 32x33 tiles.
-template <bool PAIR> __host__ __device__ constexpr int t_stage_bytes() { return TILE_A + 2 * (PAIR ? TILE_B / 2 : TILE_B); }
-template <bool PAIR> __host__ __device__ constexpr int t_run_bytes() { return PAIR ? BM * (BN + 1) * 4 : 0; }
-template <bool PAIR> __host__ __device__ constexpr int t_bar_off() { return T_STAGES * t_stage_bytes<PAIR>() + t_run_bytes<PAIR>(); }
-template <bool PAIR> __host__ __device__ constexpr int t_smem_bytes() { return t_bar_off<PAIR>() + 256 + 4 * EPI_TILE * 4 + 1024; }
+// half of the tile's B rows), then in a pair CTA the running FP32 sum of multi-chunk
+// tiles (128 rows x (BN + 1) floats, padded so that a row per lane is conflict-free),
+// the barriers, and in a single CTA the epilogue's 32x33 tiles.
+template <bool PAIR> __host__ __device__ constexpr int t_stage_bytes() {
+  return TILE_A + 2 * (t_bn<PAIR>() / (PAIR ? 2 : 1)) * BK * 4;
+}
+template <bool PAIR> __host__ __device__ constexpr int t_run_bytes() { return PAIR ? BM * (t_bn<PAIR>() + 1) * 4 : 0; }
+template <bool PAIR> __host__ __device__ constexpr int t_bar_off() { return t_stages<PAIR>() * t_stage_bytes<PAIR>() + t_run_bytes<PAIR>(); }
+template <bool PAIR> __host__ __device__ constexpr int t_smem_bytes() {
+  return t_bar_off<PAIR>() + 256 + (PAIR ? 0 : 4 * EPI_TILE * 4) + 1024;
+}
 static_assert(t_smem_bytes<false>() <= 227 * 1024 && t_smem_bytes<true>() <= 227 * 1024, "shared memory");
-constexpr uint32_t T_RUN = BN, T_ASLOT = 2 * BN;   // TMEM column bases (see the layout above)
+static_assert(2 * t_bn<true>() + 2 * 64 <= 512 && 2 * BN + 4 * 64 <= 512, "tensor memory");
+constexpr uint32_t T_RUN = BN;   // single CTA: TMEM column base of the running sum (see the layout above)
 // warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue,
 // 16 waiter; in a pair CTA 12..15 are a second set of A converters
 constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12, T_WAITER = 16;
@@ -119,9 +135,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   // TMEM, accumulator in its TMEM) and half of the tile's B columns in its shared
   // memory; rank 0 issues the M=256 MMAs for both.
   constexpr int CS = PAIR ? 2 : 1;
-  constexpr int BNH = BN / CS;                 // B rows (output columns) held by this CTA
+  constexpr int BNT = t_bn<PAIR>();            // output columns per tile
+  constexpr int BNH = BNT / CS;                // B rows (output columns) held by this CTA
   constexpr int TILE_BH = BNH * BK * 4;        // bytes
   constexpr int T_STAGE_BYTES = t_stage_bytes<PAIR>();
+  constexpr int T_STAGES = t_stages<PAIR>();
+  constexpr int NSLOT = t_aslots<PAIR>();      // A slots in TMEM (single CTA: one per stage)
   // A converter sets: each converts every NAS-th k-block, so a warp has NAS k-block
   // periods for its load/split/TMEM-store chain. In a pair CTA warps 12..15 are the
   // second set and B, halved per CTA, is converted by warps 6..7 alone.
@@ -136,14 +155,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   uint64_t* full = (uint64_t*)(smem + t_bar_off<PAIR>());
   uint64_t* bconv = full + T_STAGES;
   uint64_t* empty = bconv + T_STAGES;
-  uint64_t* aconv = empty + T_STAGES;   // [4] A slot filled (A slot = stage index; freed with the stage)
-  uint64_t* accf = aconv + 4;
+  uint64_t* aconv = empty + T_STAGES;   // [4] A slot filled
+  uint64_t* aempty = aconv + 4;         // [2] pair CTA: A slot free (MMAs of its last k-block done)
+  uint64_t* accf = aempty + 2;
   uint64_t* acce = accf + 2;
   uint64_t* drain = acce + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* epi_tiles = (float*)(smem + t_bar_off<PAIR>() + 256);
-  float* run_sum = (float*)(smem + T_STAGES * T_STAGE_BYTES);   // pair CTA: [BM][BN + 1]
+  float* run_sum = (float*)(smem + T_STAGES * T_STAGE_BYTES);   // pair CTA: [BM][BNT + 1]
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t ntiles = g.mt * g.nt * g.nsplit;
@@ -162,7 +182,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     const int64_t mt = g.m_fast ? tile % g.mt : tile / g.nt;
     const int64_t nt = g.m_fast ? tile / g.mt : tile % g.nt;
     m0 = mt * (BM * CS) + rank * BM;
-    n0 = nt * BN;
+    n0 = nt * BNT;
   };
 
   if (threadIdx.x == 0) {
@@ -173,6 +193,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     }
     for (int b = 0; b < 4; ++b) mbar_init(&aconv[b], 4 * CS);
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&aempty[b], 1);
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4 * CS);
     }
@@ -196,8 +217,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   if constexpr (PAIR) cluster_sync_all();   // the peer's barriers are initialised before any remote arrival
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  // A slots: columns [256, 512), one per stage
-  const uint32_t abase = T_ASLOT;
+  // A slots: 64 columns each (32 hi + 32 lo) from column abase
+  const uint32_t abase = t_aslot_base<PAIR>();
 
   int issued = 0;
   if (warp == 0) {
@@ -228,7 +249,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     // waiter warp does the mbarrier waits and hands each ready k-block over on a
     // named barrier, whose OR-reduction also carries an abort.
     const uint32_t idesc =
-        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((BM * CS) >> 4) << 24);
+        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BNT >> 3) << 17) | ((uint32_t)((BM * CS) >> 4) << 24);
     int it = 0, lc = 0;
     bool ok = true;
     for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
@@ -236,12 +257,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       kslice(tile, kb0, nk);
       for (int c0 = 0; c0 < nk && ok; c0 += g.kch, ++lc) {
         const int buf = lc % g.nbuf;
-        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        const uint32_t d = tmem + (uint32_t)(buf * BNT);
         const int c1 = min(nk, c0 + g.kch);
         for (int kb = c0; kb < c1; ++kb, ++it) {
           if (handoff_abort(false)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int st = it % T_STAGES, as = st;
+          const int st = it % T_STAGES, as = PAIR ? it % NSLOT : st;
           if (lane == 0) {
             const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
             const uint32_t ah = tmem + abase + (uint32_t)(as * 64), al = ah + 32;
@@ -252,7 +273,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
               mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
               mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
             }
-            mma_commit<PAIR>(&empty[st], (1u << CS) - 1);   // frees the stage and its A slot (both CTAs)
+            mma_commit<PAIR>(&empty[st], (1u << CS) - 1);   // frees the stage (both CTAs) ...
+            if constexpr (PAIR) mma_commit<PAIR>(&aempty[as], (1u << CS) - 1);   // ... and the A slot
             if (kb + 1 == c1) mma_commit<PAIR>(&accf[buf], (1u << CS) - 1);
           }
           __syncwarp();
@@ -278,11 +300,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         const int buf = lc % g.nbuf;
         const int c1 = min(nk, c0 + g.kch);
         for (int kb = c0; kb < c1; ++kb, ++it) {
-          const int st = it % T_STAGES, as = st;
+          const int st = it % T_STAGES, as = PAIR ? it % NSLOT : st;
           bool ready = true;
           if (kb == c0) ready = mbar_wait(&acce[buf], ((lc / g.nbuf) & 1) ^ 1, abort_flag);
           ready = ready && mbar_wait(&bconv[st], (it / T_STAGES) & 1, abort_flag);
-          ready = ready && mbar_wait(&aconv[as], (it / T_STAGES) & 1, abort_flag);
+          ready = ready && mbar_wait(&aconv[as], (it / NSLOT) & 1, abort_flag);
           // relay the converters' tensor-memory stores to the MMA warp
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -304,11 +326,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       kslice(tile, kb0, nk);
       for (int kb = 0; kb < nk; ++kb, ++it) {
         if (NAS > 1 && it % NAS != set) continue;
-        const int st = it % T_STAGES, as = st;
+        const int st = it % T_STAGES, as = PAIR ? it % NSLOT : st;
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-        // the slot is free once the MMAs of the stage's previous k-block are done; the TMA
-        // refill of the stage waited for the same release, so this wait passes at once
-        if (!mbar_wait(&empty[st], ((it / T_STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        // the slot is free once the MMAs of its previous k-block are done. Single CTA: the
+        // slot is the stage's, and the TMA refill of the stage waited for the same release,
+        // so this wait passes at once; pair CTA: the A-slot ring of its own (two back)
+        if (PAIR ? !mbar_wait(&aempty[as], ((it / NSLOT) & 1) ^ 1, abort_flag)
+                 : !mbar_wait(&empty[st], ((it / T_STAGES) & 1) ^ 1, abort_flag)) {
+          ok = false;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint4* row = (const uint4*)(A_f(st) + r * 128);
         float hi[32], lo[32];
@@ -380,16 +407,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         if (!mbar_wait(&accf[buf], (lc / g.nbuf) & 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-        for (int cb = 0; cb < BN; cb += 32) {
+        for (int cb = 0; cb < BNT; cb += 32) {
           float v[32];
           uint32_t rc[32], rr[32];
-          tmem_ld32_async(tmem + lane_base + (uint32_t)(buf * BN + cb), rc);
+          tmem_ld32_async(tmem + lane_base + (uint32_t)(buf * BNT + cb), rc);
           if (ch == 0) {
             tmem_wait32(rc);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rc[j]);
           } else if constexpr (PAIR) {
-            const float* rs = run_sum + (q * 32 + lane) * (BN + 1) + cb;
+            const float* rs = run_sum + (q * 32 + lane) * (BNT + 1) + cb;
             tmem_wait32(rc);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = rs[j] + __uint_as_float(rc[j]);
@@ -402,7 +429,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
           }
           if (ch + 1 < nch) {
             if constexpr (PAIR) {
-              float* rs = run_sum + (q * 32 + lane) * (BN + 1) + cb;
+              float* rs = run_sum + (q * 32 + lane) * (BNT + 1) + cb;
 #pragma unroll
               for (int j = 0; j < 32; ++j) rs[j] = v[j];
             } else {
@@ -410,9 +437,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             }
           } else if (!__shfl_sync(0xffffffffu, *abort_flag, 0)) {   // warp-uniform decision
             if (g.nsplit > 1 || g.om.c3 == 1) {
-              float* tw = epi_tiles + q * EPI_TILE;
+              // staging of this warp's 32 x 32 block: its own rows of the running sum in a pair
+              // CTA (the tile's last use of them), else the warp's epilogue tile
+              constexpr int TS = PAIR ? BNT + 1 : 33;
+              float* tw = PAIR ? run_sum + (q * 32) * TS + cb : epi_tiles + q * EPI_TILE;
 #pragma unroll
-              for (int j = 0; j < 32; ++j) tw[lane * 33 + j] = v[j];
+              for (int j = 0; j < 32; ++j) tw[lane * TS + j] = v[j];
               __syncwarp();
               const int64_t n = n0 + cb + lane;
               const bool ncol = n < g.N;
@@ -420,14 +450,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
                 float* pbase = g.part + (tile / (g.mt * g.nt)) * g.M * g.N + n;
                 for (int r = 0; r < 32; ++r) {
                   const int64_t mr = m0 + q * 32 + r;
-                  if (mr < g.M && ncol) pbase[mr * g.N] = tw[r * 33 + lane];
+                  if (mr < g.M && ncol) pbase[mr * g.N] = tw[r * TS + lane];
                 }
               } else {
                 const int64_t no = ncol ? (n / g.om.ndiv) * g.om.c2 + (n % g.om.ndiv) : 0;
                 for (int r = 0; r < 32; ++r) {
                   const int64_t mor = __shfl_sync(0xffffffffu, mo, r);
                   const int64_t mr = m0 + q * 32 + r;
-                  if (mr < g.M && ncol) g.C[mor + no] = tw[r * 33 + lane];
+                  if (mr < g.M && ncol) g.C[mor + no] = tw[r * TS + lane];
                 }
               }
               __syncwarp();
@@ -597,7 +627,7 @@ static Plan plan_of(int64_t M, int64_t N, int64_t K) {
   const int cs = p.pair ? 2 : 1;
   p.slots = p.pair ? pair_slots() : sm_count();
   p.mt = (M + BM * cs - 1) / (BM * cs);
-  p.nt = (N + BN - 1) / BN;
+  p.nt = (N + (p.pair ? t_bn<true>() : BN) - 1) / (p.pair ? t_bn<true>() : BN);
   const int64_t nk = (K + BK - 1) / BK;
   const int ns = nsplit_of(p.mt * p.nt, K, (int)p.slots);
   p.ks = (int)((nk + ns - 1) / ns);
@@ -623,7 +653,7 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
   }
   const Plan p = plan_of(M, N, K);
   CUtensorMap ma = make_map(A, M, K, lda, BM);
-  CUtensorMap mb = make_map(B, N, K, ldb, p.pair ? BN / 2 : BN);
+  CUtensorMap mb = make_map(B, N, K, ldb, p.pair ? t_bn<true>() / 2 : BN);
   TcArgs g;
   g.M = M; g.N = N; g.K = K; g.om = om; g.C = C; g.err = (int*)scratch;
   g.mt = p.mt;

@@ -41,15 +41,7 @@ class RowWorkload:
 
 
 def hubbard_row(name, Lx, Ly, D, chi, row, K=4, seed=0, p=4) -> RowWorkload:
-    peps = L.random_peps(Lx, Ly, D, p, seed=seed)
-    ham = L.hubbard_hamiltonian(Lx, Ly, seed=seed, K=K) if p == 4 else L.random_hamiltonian(Lx, Ly, p, K, seed)
-    pepo = L.fsm_pepo(ham)
-    B = D * (K + 2) * D
-    bonds = L.boundary_bond_profile(Ly, chi, B)
-    phys = [(1 if False else D) * (K + 2) * D for _ in range(Ly)]
-    # up-bundle of row `row` site c: D*w*D (edges have D=1 on horizontal legs only)
-    phys = [peps[row][c].shape[1] * pepo[row][c].shape[1] * peps[row][c].shape[1] for c in range(Ly)]
-    bnd = L.random_boundary(bonds, phys, seed=seed + 1000 * row, dtype=np.float64)
+    peps, pepo, bnd = L.interior_row_inputs(Lx, Ly, D, chi, row, K, seed, p)
     return RowWorkload(name, Lx, Ly, D, p, K, chi, row, peps, pepo, bnd)
 
 

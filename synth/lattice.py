@@ -294,6 +294,22 @@ def boundary_bond_profile(Ly: int, chi: int, bundle: int):
     return bonds
 
 
+def interior_row_inputs(Lx: int, Ly: int, D: int, chi: int, row: int, K: int, seed: int, p: int = 4):
+    """Inputs of one interior-row absorption: (peps, pepo, boundary).
+
+    Random PEPS (seed), the Hubbard-shaped FSM PEPO with K hopping channels (p = 4; a
+    random Hamiltonian otherwise) and a random boundary MPS with the bond profile of a
+    top-to-bottom sweep, bond bundle D (K + 2) D, physical bundles those of ``row``.
+    """
+    peps = random_peps(Lx, Ly, D, p, seed=seed)
+    ham = hubbard_hamiltonian(Lx, Ly, seed=seed, K=K) if p == 4 else random_hamiltonian(Lx, Ly, p, K, seed)
+    pepo = fsm_pepo(ham)
+    bonds = boundary_bond_profile(Ly, chi, D * (K + 2) * D)
+    phys = [peps[row][c].shape[1] * pepo[row][c].shape[1] * peps[row][c].shape[1] for c in range(Ly)]
+    bnd = random_boundary(bonds, phys, seed=seed + 1000 * row, dtype=np.float64)
+    return peps, pepo, bnd
+
+
 def pack_lattice(tensors, dtype=np.float64) -> np.ndarray:
     """Concatenate site tensors (row-major site order, each C-contiguous) into one flat buffer."""
     return np.concatenate([np.ascontiguousarray(t, dtype=dtype).ravel() for row in tensors for t in row])

@@ -8,8 +8,13 @@ Configurations (seeded synthetic inputs, no paper data):
   c3_fsm[_decay] 6x6, D=6, p=4, FSM PEPO w=4 (K=2, random symmetric h, X, Y), chi=256,
                 oversample 10, q=2, n_fit=1: <psi|H|psi> and <psi|psi> by full sweeps,
                 the log-scale of every compressed row and the kept spectra of row 2.
-Usage: python tests/golden/make_golden.py [--decay] [--c3] [seeds...]
-       -> tests/golden/c2_fsm[_decay]_seed{S}.json, c3_fsm[_decay]_seed{S}.json
+  c3_row2       6x6, D=6, p=4, Hubbard-shaped FSM PEPO w=4 (K=2), chi=256: row 2 absorbed
+                into a seeded random boundary MPS (bond profile of a top-down sweep),
+                zip-up rSVD (oversample 10, q=2) + one CBE fit pass: the row's log-scale,
+                the zip-up and fit spectra of every bond.
+Usage: python tests/golden/make_golden.py [--decay] [--c3 | --c3row] [seeds...]
+       -> tests/golden/c2_fsm[_decay]_seed{S}.json, c3_fsm[_decay]_seed{S}.json,
+          c3_row2_seed{S}.json
 """
 import json
 import os
@@ -66,13 +71,40 @@ def c3(seed: int, sketch_seed: int = 1, decay: bool = False):
     }
 
 
+def c3row(seed: int, sketch_seed: int = 1):
+    Lx, Ly, D, chi, row, K = 6, 6, 6, 256, 2, 2
+    peps, pepo, bnd = L.interior_row_inputs(Lx, Ly, D, chi, row, K, seed)
+    prm = B.RsvdParams(oversample=10, power_iters=2, n_fit=1)
+    t0 = time.time()
+    res = B.absorb_row(bnd, peps[row], pepo[row], chi, prm, seed=sketch_seed, layer=1, row=row)
+    return {
+        "config": "6x6 D=6 p=4 Hubbard FSM w=4 (K=2) chi=256, row 2 into a seeded boundary, "
+                  "oversample=10 q=2 n_fit=1",
+        "Lx": Lx, "Ly": Ly, "D": D, "chi": chi, "row": row, "K": K,
+        "input_seed": seed, "sketch_seed": sketch_seed,
+        "boundary_bonds": [int(bnd[0].shape[0])] + [int(t.shape[2]) for t in bnd],
+        "log_scale": float(res.log_scale),
+        "zip_spectra": [list(map(float, s)) for s in res.zip_spectra],
+        "fit_spectra": [list(map(float, s)) for s in res.fit_spectra],
+        "new_bonds": [int(res.T[0].shape[0])] + [int(t.shape[2]) for t in res.T],
+        "oracle_seconds": time.time() - t0,
+    }
+
+
 if __name__ == "__main__":
     here = os.path.dirname(os.path.abspath(__file__))
     args = sys.argv[1:]
     decay = "--decay" in args
     big = "--c3" in args
-    args = [a for a in args if a not in ("--decay", "--c3")]
+    one_row = "--c3row" in args
+    args = [a for a in args if a not in ("--decay", "--c3", "--c3row")]
     for s in [int(x) for x in (args or ["0"])]:
+        if one_row:
+            out = c3row(s)
+            with open(os.path.join(here, f"c3_row2_seed{s}.json"), "w") as f:
+                json.dump(out, f, indent=1)
+            print(s, out["log_scale"], out["oracle_seconds"])
+            continue
         out = (c3 if big else c2)(s, decay=decay)
         stem = "c3_fsm" if big else "c2_fsm"
         name = f"{stem}_decay_seed{s}.json" if decay else f"{stem}_seed{s}.json"

@@ -257,3 +257,49 @@ def test_k_column_slicing_c2_stored_oracle(fp, monkeypatch, prec, tol):
     env.close()
     assert sn == gold["num_sign"]
     assert abs(ln - gold["num_log"]) < tol
+
+
+C3ROW = os.path.join(HERE, "golden", "c3_row2_seed0.json")
+
+
+def _c3_row2(fp, prec):
+    """Row 2 of the 6x6, D=6, w=4, chi=256 lattice absorbed into the stored seeded boundary:
+    (log-scale, zip-up spectra, fit spectra) of the GPU path."""
+    from paper_2511_01039_gb300 import workloads as WL
+    gold = json.load(open(C3ROW))
+    peps, pepo, bnd = L.interior_row_inputs(gold["Lx"], gold["Ly"], gold["D"], gold["chi"], gold["row"], gold["K"],
+                                            gold["input_seed"])
+    env = _env(fp, peps, pepo, D=gold["D"], w=gold["K"] + 2, chi=gold["chi"], prec=prec, seed=gold["sketch_seed"])
+    fp.fpeps_import_boundary(env.h, WL.boundary_blob(bnd, gold["row"], 1, 8 if prec == "f64" else 4), gold["row"], 1)
+    fp.fpeps_absorb_row(env.h, gold["row"], 1)
+    st = fp.fpeps_compress_rsvd(env.h, fp.params(10, 2, 0, 1, 0))
+    nb = gold["Ly"] - 1
+    zs = [np.array(fp.fpeps_bond_spectrum(env.h, 0, c)) for c in range(nb)]
+    fs = [np.array(fp.fpeps_bond_spectrum(env.h, 1, c)) for c in range(nb)]
+    env.close()
+    return gold, st.log_scale, zs, fs
+
+
+def _spec_err(got, ref):
+    """Largest deviation of a kept spectrum, relative to its largest value."""
+    ref = np.asarray(ref)
+    assert got.shape == ref.shape
+    return float(np.max(np.abs(got - ref)) / ref.max())
+
+
+@pytest.mark.skipif(not os.path.exists(C3ROW), reason="stored C3 row not written (tests/golden/make_golden.py --c3row)")
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 1e-4), ("tf32x3", 1e-4)])
+def test_c3_row2_against_stored_oracle(fp, prec, tol):
+    """6x6, D=6, w=4 (Hubbard-shaped FSM), chi=256: row 2 absorbed into a seeded boundary MPS by
+    the zip-up rSVD and one CBE fit pass (Sec. IV), against the FP64 oracle's stored result:
+    the row's log-scale and the kept spectrum of every bond after the zip-up and after the fit.
+    FP64 must agree to 1e-8; the FP32 and 3xTF32 paths are held to 1e-4 (FP32 rounding amplified
+    through the chained factorisations of one row)."""
+    gold, ls, zs, fs = _c3_row2(fp, prec)
+    errs = {"log_scale": abs(ls - gold["log_scale"]),
+            "zip": max(_spec_err(z, r) for z, r in zip(zs, gold["zip_spectra"])),
+            "fit": max(_spec_err(f, r) for f, r in zip(fs, gold["fit_spectra"]))}
+    print(f"C3 row 2 {prec}: {errs}")
+    assert errs["log_scale"] < tol
+    assert errs["zip"] < tol
+    assert errs["fit"] < tol
