@@ -84,8 +84,9 @@ struct TcArgs {
 // FP32 sum; [256,512) four A slots of 32 hi + 32 lo columns, one per stage. A pair
 // CTA: below. Warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters (TMEM lane
 // quarter = warp % 4), 6..7 and 12..15 B converters (in a pair CTA 12..15 are a
-// second set of A converters), 8..11 epilogue, 16 barrier waiter for the MMA warp.
-constexpr int P_THREADS = 544;
+// second set of A converters), 8..11 epilogue, 16 barrier waiter for the MMA warp,
+// 17..18 two more B converters (pair CTA; idle in a single CTA).
+constexpr int P_THREADS = 608;
 // Pair tiles are 256 x 192 (N = 192 per MMA): a tcgen05.mma costs its issuing thread a
 // fixed ~58 ns (~120 SM cycles at 2.07 GHz, measured on GB300, M = 128 per SM, kind::tf32)
 // for any N up to ~200, while an N = 128 pair MMA gives each SM only ~70 cycles of tensor
@@ -113,8 +114,8 @@ static_assert(t_smem_bytes<false>() <= 227 * 1024 && t_smem_bytes<true>() <= 227
 static_assert(2 * t_bn<true>() + 2 * 64 <= 512 && 2 * BN + 4 * 64 <= 512, "tensor memory");
 constexpr uint32_t T_RUN = BN;   // single CTA: TMEM column base of the running sum (see the layout above)
 // warps: 0 TMA, 1 TMEM + MMA, 2..5 A converters, 6..7 and 12..15 B converters, 8..11 epilogue,
-// 16 waiter; in a pair CTA 12..15 are a second set of A converters
-constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12, T_WAITER = 16;
+// 16 waiter, 17..18 B converters (pair); in a pair CTA 12..15 are a second set of A converters
+constexpr int T_BCONV0 = 6, T_NBCONV = 6, T_EPI0 = 8, T_BCONV1 = 12, T_WAITER = 16, T_BCONV2 = 17;
 
 // named barrier 1 between the MMA warp and the waiter warp (64 threads); returns
 // true if any participating thread passed true
@@ -143,9 +144,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   constexpr int NSLOT = t_aslots<PAIR>();      // A slots in TMEM (single CTA: one per stage)
   // A converter sets: each converts every NAS-th k-block, so a warp has NAS k-block
   // periods for its load/split/TMEM-store chain. In a pair CTA warps 12..15 are the
-  // second set and B, halved per CTA, is converted by warps 6..7 alone.
+  // second set and B, halved per CTA, is converted by warps 6..7 and 17..18.
   constexpr int NAS = PAIR ? 2 : 1;
-  constexpr int NBW = PAIR ? 2 : T_NBCONV;
+  constexpr int NBW = PAIR ? 4 : T_NBCONV;
   const uint32_t rank = PAIR ? cluster_rank() : 0;
   const bool issuer = rank == 0;
   // a CTA pair may not split up on a shared early exit, so only single CTAs return here
@@ -359,9 +360,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         if (lane == 0) mbar_arrive_issuer<PAIR>(&aconv[as], rank);
       }
     }
-  } else if ((warp >= T_BCONV0 && warp < T_EPI0) || (!PAIR && warp >= T_BCONV1 && warp < T_WAITER)) {
+  } else if ((warp >= T_BCONV0 && warp < T_EPI0) || (!PAIR && warp >= T_BCONV1 && warp < T_WAITER) ||
+             (PAIR && warp >= T_BCONV2 && warp < T_BCONV2 + 2)) {
     // B converters: hi in place, lo into the second B tile
-    const int cw = warp < T_EPI0 ? warp - T_BCONV0 : warp - T_BCONV1 + (T_EPI0 - T_BCONV0);
+    const int cw = warp < T_EPI0 ? warp - T_BCONV0
+                                 : (PAIR ? warp - T_BCONV2 : warp - T_BCONV1) + (T_EPI0 - T_BCONV0);
     int it = 0;
     bool ok = true;
     for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
