@@ -225,8 +225,11 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ double D[CH_NB][CH_NB + 1];
+  __shared__ double inv_s[CH_NB];
+  __shared__ double rinv_s;
   __shared__ int bad_s;
   const int tid = threadIdx.x;
+  const int lane = tid % 32, warp = tid / 32;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + tid;
   const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
   if (blockIdx.x == 0 && tid == 0) {
@@ -250,14 +253,18 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
       if (tid == 0) bad_s = 0;
       __syncthreads();
       for (int j = 0; j < nb; ++j) {
+        // FP64 sqrt and division are long latencies here (~680 / ~430 cycles): the pivot's
+        // sqrt and the row's scale factor rsqrt run side by side
         if (tid == 0) {
           const double d = D[j][j];
           if (!isfinite(d)) bad_s = 1;
-          D[j][j] = d > tol * dmax ? sqrt(d) : 0.0;
+          const bool keep = d > tol * dmax;
+          D[j][j] = keep ? sqrt(d) : 0.0;
+          rinv_s = keep ? rsqrt(d) : 0.0;
         }
         __syncthreads();
         if (bad_s) break;
-        for (int c = j + 1 + tid; c < nb; c += blockDim.x) D[j][c] = D[j][j] > 0 ? D[j][c] / D[j][j] : 0.0;
+        for (int c = j + 1 + tid; c < nb; c += blockDim.x) D[j][c] *= rinv_s;
         __syncthreads();
         const int n = nb - j - 1;
         for (int e = tid; e < n * n; e += blockDim.x) {
@@ -274,24 +281,46 @@ __global__ void __launch_bounds__(256) k_cholesky_coop(double* G, int k, double 
     }
     grid.sync();
     if (*(volatile int*)info) return;
-    // panel row: R[p0:p0+nb, c] solves R_pp^T x = G[p0:p0+nb, c] for c >= p0 + nb
-    for (int64_t c = p0 + nb + gtid; c < k; c += gsize) {
-      for (int i = 0; i < nb; ++i) {
-        double x = G[(int64_t)(p0 + i) * k + c];
-        for (int l = 0; l < i; ++l) x -= G[(int64_t)(p0 + l) * k + p0 + i] * G[(int64_t)(p0 + l) * k + c];
-        const double piv = G[(int64_t)(p0 + i) * k + p0 + i];
-        G[(int64_t)(p0 + i) * k + c] = piv > 0 ? x / piv : 0.0;
+    // panel row: R[p0:p0+nb, c] solves R_pp^T x = G[p0:p0+nb, c] for c >= p0 + nb, one warp
+    // per column spread over the whole grid (lane i holds row i; each solved value is
+    // broadcast and folded into the rows below it), every block with the factored diagonal
+    // block and its pivots' reciprocals in shared memory
+    for (int e = tid; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = G[(int64_t)(p0 + e / nb) * k + p0 + e % nb];
+    __syncthreads();
+    for (int i = tid; i < nb; i += blockDim.x) inv_s[i] = D[i][i] > 0 ? 1.0 / D[i][i] : 0.0;
+    __syncthreads();
+    {
+      const int wpb = blockDim.x / 32;
+      for (int64_t c = p0 + nb + (int64_t)blockIdx.x * wpb + warp; c < k; c += (int64_t)gridDim.x * wpb) {
+        const double gl = lane < nb ? G[(int64_t)(p0 + lane) * k + c] : 0.0;
+        double acc = 0.0, mine = 0.0;
+        for (int l = 0; l < nb; ++l) {
+          double r = 0.0;
+          if (lane == l) r = inv_s[l] != 0.0 ? (gl - acc) * inv_s[l] : 0.0;
+          r = __shfl_sync(0xffffffffu, r, l);
+          if (lane == l) mine = r;
+          if (lane > l && lane < nb) acc = fma(D[l][lane], r, acc);
+        }
+        if (lane < nb) G[(int64_t)(p0 + lane) * k + c] = mine;
       }
     }
     grid.sync();
-    // trailing update of the upper triangle
+    // trailing update of the upper triangle (four partial sums: the dependent FP64 FMA
+    // chain is 64 cycles per step)
     const int64_t r0 = p0 + nb, n = k - r0;
     for (int64_t e = gtid; e < n * n; e += gsize) {
       const int64_t i = r0 + e / n, c = r0 + e % n;
       if (c < i) continue;
-      double acc = 0;
-      for (int l = 0; l < nb; ++l) acc = fma(G[(int64_t)(p0 + l) * k + i], G[(int64_t)(p0 + l) * k + c], acc);
-      G[i * k + c] -= acc;
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int l = 0;
+      for (; l + 4 <= nb; l += 4) {
+        a0 = fma(G[(int64_t)(p0 + l) * k + i], G[(int64_t)(p0 + l) * k + c], a0);
+        a1 = fma(G[(int64_t)(p0 + l + 1) * k + i], G[(int64_t)(p0 + l + 1) * k + c], a1);
+        a2 = fma(G[(int64_t)(p0 + l + 2) * k + i], G[(int64_t)(p0 + l + 2) * k + c], a2);
+        a3 = fma(G[(int64_t)(p0 + l + 3) * k + i], G[(int64_t)(p0 + l + 3) * k + c], a3);
+      }
+      for (; l < nb; ++l) a0 = fma(G[(int64_t)(p0 + l) * k + i], G[(int64_t)(p0 + l) * k + c], a0);
+      G[i * k + c] -= (a0 + a1) + (a2 + a3);
     }
     grid.sync();
   }
