@@ -1,8 +1,9 @@
 """Kernel-level parity through the C ABI (fpeps_gemm_f32): the tensor-core
 3xTF32 GEMM and the CUDA-core FP32 GEMM against an FP64 evaluation of the same
-product, on ragged shapes that span several 128x128x32 tiles. Products with
-M <= 128 run on single CTAs, larger ones on CTA pairs (256-row tiles); M = 129
-and 257 leave most rows of a pair's second CTA outside the matrix."""
+product, on ragged shapes that span several tiles. Products with M <= 128 run on
+single CTAs (128x128 tiles), larger ones on CTA pairs (256x192 tiles); M = 129
+and 257 leave most rows of a pair's second CTA outside the matrix, and N = 260,
+300, 2000, 4097 (or N < 192) leave a partial last column tile of a pair."""
 import pytest
 
 pytestmark = pytest.mark.gpu
