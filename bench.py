@@ -11,8 +11,9 @@ The metric is algorithmic TFLOP/s of the contractions (the Fig. 2(a)
 applications; QR/SVD flops are not counted), the e2e number the same through
 host buffers (H2D of the boundary, D2H of the new boundary inside the timed
 region). The line also carries the plain FP32 path on the same row
-(fp32_path) and the relative errors of norm and energy against the stored FP64
-oracle values of the 6x6, D=6, chi=256 lattice (rel_err_vs_fp64).
+(fp32_path) and the relative errors against stored FP64 oracle values
+(rel_err_vs_fp64): norm, numerator and energy of the 4x4, D=4, chi=64 lattice,
+and the log-scale and kept spectra of row 2 of the 6x6, D=6, chi=256 lattice.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|f32|f64]
   python bench.py --impl reference ...   (the FP64 oracle on the host cores)
@@ -313,33 +314,67 @@ def timed_steps(fp, env, blob_ptr, nbytes, row, prm, steps):
 
 
 def accuracy_record(precs=("tf32x3", "f32")):
-    """Relative errors of <psi|H|psi>, <psi|psi> and <H> of the 6x6, D=6, w=4, chi=256 lattice
-    (full sweeps, zip-up rSVD + CBE fit) against the stored FP64 oracle values
-    (tests/golden/c3_fsm_seed0.json, written by tests/golden/make_golden.py), per precision."""
+    """Relative errors against stored FP64 oracle values (written by tests/golden/make_golden.py),
+    per precision:
+      * C2, 4x4 D=4 w=4 chi=64 (full sweeps, zip-up rSVD + CBE fit), random and decaying PEPS:
+        <psi|psi>, <psi|H|psi> and <H>;
+      * C3, 6x6 D=6 w=4 chi=256, row 2 absorbed into a seeded boundary: the row's log-scale
+        (absolute difference) and the largest deviation of any bond's kept spectrum after the
+        zip-up and after the fit, relative to that spectrum's largest value."""
     import math
 
+    import numpy as np
     from paper_2511_01039_gb300 import fpeps as fp
+    from paper_2511_01039_gb300 import workloads as WL
     from synth import lattice as L
-    path = os.path.join(ROOT, "tests", "golden", "c3_fsm_seed0.json")
-    if not os.path.exists(path):
-        return None
-    gold = json.load(open(path))
-    peps = L.random_peps(6, 6, 6, 4, seed=gold["peps_seed"])
-    pepo = L.fsm_pepo(L.random_hamiltonian(6, 6, 4, 2, seed=gold["ham_seed"]))
-    e_ref = gold["num_sign"] * gold["den_sign"] * math.exp(gold["num_log"] - gold["den_log"])
-    out = {"workload": gold["config"], "reference": "FP64 oracle (numpy), stored", "by_precision": {}}
-    for prec in precs:
-        env = fp.Env(peps, pepo, D=6, p=4, w=4, chi=256, prec=prec, seed=gold["sketch_seed"])
-        t0 = time.perf_counter()
-        val, sn, ln = env.expect(fp.params(10, 2, 0, 1, 0))   # operator sweep, then the norm sweep
-        el = time.perf_counter() - t0
-        sd, ld = fp.fpeps_sweep_value(env.h)                    # the norm sweep's value
-        env.close()
-        out["by_precision"][prec] = {
-            "norm": abs(math.exp(ld - gold["den_log"]) - 1) if sd == gold["den_sign"] else 2.0,
-            "numerator": abs(math.exp(ln - gold["num_log"]) - 1) if sn == gold["num_sign"] else 2.0,
-            "energy": abs(val / e_ref - 1),
-            "seconds_both_sweeps": el}
+    gdir = os.path.join(ROOT, "tests", "golden")
+    out = {"reference": "FP64 oracle (numpy), stored values", "c2": {}, "c3_row2": None}
+    for decay in (False, True):
+        path = os.path.join(gdir, "c2_fsm_decay_seed0.json" if decay else "c2_fsm_seed0.json")
+        if not os.path.exists(path):
+            continue
+        gold = json.load(open(path))
+        peps = (L.decaying_peps if decay else L.random_peps)(4, 4, 4, 4, seed=gold["peps_seed"])
+        pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=gold["ham_seed"]))
+        e_ref = gold["num_sign"] * gold["den_sign"] * math.exp(gold["num_log"] - gold["den_log"])
+        rec = {"workload": gold["config"]}
+        for prec in precs:
+            env = fp.Env(peps, pepo, D=4, p=4, w=4, chi=64, prec=prec, seed=gold["sketch_seed"])
+            val, sn, ln = env.expect(fp.params(10, 2, 0, 1, 0))   # operator sweep, then the norm sweep
+            sd, ld = fp.fpeps_sweep_value(env.h)
+            env.close()
+            rec[prec] = {"norm": abs(math.exp(ld - gold["den_log"]) - 1) if sd == gold["den_sign"] else 2.0,
+                         "numerator": abs(math.exp(ln - gold["num_log"]) - 1) if sn == gold["num_sign"] else 2.0,
+                         "energy": abs(val / e_ref - 1)}
+        out["c2"]["decaying" if decay else "random"] = rec
+    path = os.path.join(gdir, "c3_row2_seed0.json")
+    if os.path.exists(path):
+        gold = json.load(open(path))
+        peps, pepo, bnd = L.interior_row_inputs(gold["Lx"], gold["Ly"], gold["D"], gold["chi"], gold["row"],
+                                                gold["K"], gold["input_seed"])
+        rec = {"workload": gold["config"]}
+        for prec in precs:
+            env = fp.Env(peps, pepo, D=gold["D"], p=4, w=gold["K"] + 2, chi=gold["chi"], prec=prec,
+                         seed=gold["sketch_seed"])
+            fp.fpeps_import_boundary(env.h, WL.boundary_blob(bnd, gold["row"], 1, 4), gold["row"], 1)
+            t0 = time.perf_counter()
+            fp.fpeps_absorb_row(env.h, gold["row"], 1)
+            st = fp.fpeps_compress_rsvd(env.h, fp.params(10, 2, 0, 1, 0))
+            el = time.perf_counter() - t0
+            nb = gold["Ly"] - 1
+
+            def dev(which, ref):
+                worst = 0.0
+                for c in range(nb):
+                    sv = np.array(fp.fpeps_bond_spectrum(env.h, which, c))
+                    r = np.asarray(ref[c])
+                    worst = max(worst, float(np.max(np.abs(sv - r)) / r.max()) if sv.shape == r.shape else 2.0)
+                return worst
+            rec[prec] = {"log_scale_abs": abs(st.log_scale - gold["log_scale"]),
+                         "zip_spectra": dev(0, gold["zip_spectra"]), "fit_spectra": dev(1, gold["fit_spectra"]),
+                         "seconds_row": el}
+            env.close()
+        out["c3_row2"] = rec
     return out
 
 
