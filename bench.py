@@ -9,8 +9,8 @@ timing, by sweeping rows 0-3 of the same seeded lattice through the library
 (--boundary random: a seeded random boundary of the same bond profile instead).
 The metric is algorithmic TFLOP/s of the contractions (the Fig. 2(a)
 applications; QR/SVD flops are not counted), the e2e number the same through
-host buffers (H2D of the boundary, D2H of the new boundary inside the timed
-region). The line also carries the plain FP32 path on the same row
+pinned host buffers (H2D of the boundary, D2H of the new boundary inside the
+timed region). The line also carries the plain FP32 path on the same row
 (fp32_path) and the relative errors against stored FP64 oracle values
 (rel_err_vs_fp64): norm, numerator and energy of the 4x4, D=4, chi=64 lattice,
 and the log-scale and kept spectra of row 2 of the 6x6, D=6, chi=256 lattice.
@@ -475,6 +475,14 @@ def main():
     # ---------------- end to end through host buffers
     e2e = None
     if not args.no_e2e:
+        # the checkpoint and the new boundary in pinned host buffers, allocated before timing
+        import numpy as np
+        lib = fp.lib()
+        hin = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+        hin.numpy()[:] = np.frombuffer(blob, dtype=np.uint8)
+        nout = fp.C.c_size_t(0)
+        fp._check(env.h, lib.fpeps_export_boundary(env.h, None, fp.C.byref(nout)))
+        hout = torch.empty(nout.value, dtype=torch.uint8, pin_memory=True)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -482,9 +490,10 @@ def main():
         ef = 0.0
         d2h = 0
         for _ in range(args.steps):
-            st = step(fp.C.cast(fp.C.c_char_p(blob), fp.C.c_void_p).value, len(blob))
-            out = fp.fpeps_export_boundary(env.h)
-            d2h = len(out)
+            st = step(hin.data_ptr(), len(blob))
+            n = fp.C.c_size_t(nout.value)
+            fp._check(env.h, lib.fpeps_export_boundary(env.h, fp.C.c_void_p(hout.data_ptr()), fp.C.byref(n)))
+            d2h = n.value
             ef += st.alg_flops
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
