@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "f32", "f64"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "bf16x3", "f32", "f64"])
     ap.add_argument("--workload", default="C4", choices=["C3", "C4"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -193,15 +193,19 @@ def roofline_of(kind: str, d: dict, prec: str, peaks: dict) -> dict:
     if kind in DRAM_PER_ALG_BYTE and d["launches"]:
         traffic = DRAM_PER_ALG_BYTE[kind] * d["bytes"] / d["launches"]
     intensity = d["flops"] / d["bytes"] if d["bytes"] > 0 else float("inf")   # flop per byte
-    tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if prec == "tf32x3" else ("gemm_tc_tf32x3",)
+    tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if prec in ("tf32x3", "bf16x3") else ("gemm_tc_tf32x3",)
     if kind in tensor_kinds:
-        peak = bf16 * 1.1 / 2.25               # TF32 dense peak = BF16 x nominal TF32/BF16 ratio
+        # 3xBF16 GEMMs against the BF16 peak; 3xTF32 (and the sandwich in either mode) against the
+        # TF32 dense peak = BF16 x nominal TF32/BF16 ratio
+        bfk = prec == "bf16x3" and kind == "gemm_tc_tf32x3"
+        peak = bf16 if bfk else bf16 * 1.1 / 2.25
         ridge = (peak / 3.0) * 1e12 / (hbm * 1e9)
         if intensity >= ridge:
+            what = f"BF16 peak {src}" if bfk else f"TF32 peak = {src} BF16 x 1.1/2.25"
             return {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
                     "traffic": traffic, "kernel": kind,
-                    "note": f"TF32 peak = {src} BF16 x 1.1/2.25; algorithmic flops, and 3xTF32 issues 3 MMAs per "
-                            f"product, so frac <= 1/3"}
+                    "note": f"{what}; algorithmic flops, and a 3-way split issues 3 MMAs per product, so "
+                            f"frac <= 1/3"}
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
                 "kernel": kind,
                 "note": f"{intensity:.1f} algorithmic flop/byte, below the 3xTF32 ridge of {ridge:.1f} flop/byte "
@@ -313,7 +317,7 @@ def timed_steps(fp, env, blob_ptr, nbytes, row, prm, steps):
     return e0.elapsed_time(e1), flops
 
 
-def accuracy_record(precs=("tf32x3", "f32")):
+def accuracy_record(precs=("tf32x3", "bf16x3", "f32")):
     """Relative errors against stored FP64 oracle values (written by tests/golden/make_golden.py),
     per precision:
       * C2, 4x4 D=4 w=4 chi=64 (full sweeps, zip-up rSVD + CBE fit), random and decaying PEPS:
@@ -537,7 +541,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world if dist else args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "seconds_per_row": ms / args.steps / 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 data, 3xTF32 tensor-core products" if args.prec == "tf32x3" else args.prec,
+            "vs_baseline": None, "dtype": {"tf32x3": "f32 data, 3xTF32 tensor-core products",
+                      "bf16x3": "f32 data, 3xBF16 tensor-core GEMMs, 3xTF32 sandwich"}.get(args.prec, args.prec),
             "data": "synthetic (seeded PEPS, Hubbard-shaped PEPO; input boundary " +
                     ("swept from rows 0-3 of the same lattice by the library)" if args.boundary == "sweep"
                      else "seeded random)"),

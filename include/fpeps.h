@@ -55,7 +55,10 @@ typedef enum {
 /* Arithmetic of the contraction GEMMs (the QR and the small SVD always run in
  * FP64-class precision). FP64: everything in double. F32: plain FP32 CUDA-core
  * products. TF32X3 / BF16X3: split-precision products on the tensor cores,
- * a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with FP32 accumulation. */
+ * a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with FP32 accumulation, the operands split
+ * into TF32 (3 x 2^-22 relative error per product) or BF16 (3 x 2^-16) halves.
+ * In BF16X3 the boundary and environment GEMMs take the BF16 split; the site
+ * sandwich and the tall products of the QR stay 3xTF32 / FP32. */
 typedef enum { FPEPS_F64 = 0, FPEPS_F32 = 1, FPEPS_TF32X3 = 2, FPEPS_BF16X3 = 3 } fpeps_precision;
 
 /* Device-memory provider. alloc(ctx, bytes, stream) returns device memory usable
@@ -122,8 +125,7 @@ typedef struct fpeps_env fpeps_env;
  * The inputs are copied (and converted to the compute precision) before the
  * call returns; the caller keeps ownership of its buffers.
  * Errors: FPEPS_ERR_ARG (bad sizes/pointers), FPEPS_ERR_OOM, FPEPS_ERR_CUDA,
- * FPEPS_ERR_UNSUPPORTED (n_envs != 1, or prec == FPEPS_BF16X3, whose kernels
- * are not built); FPEPS_ERR_ARG also when symmetry is not 0 or 1 or charges_host
+ * FPEPS_ERR_UNSUPPORTED (n_envs != 1); FPEPS_ERR_ARG also when symmetry is not 0 or 1 or charges_host
  * does not match it. */
 fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, const void* pepo_dev,
                               const int32_t* charges_host, int32_t dtype_in, void* cuda_stream,
@@ -233,9 +235,10 @@ fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void*
 
 /* One contraction GEMM of the path on caller device buffers (diagnostic):
  * C[M][N] (row-major) = sum_k A[m][k] B[n][k]; A [M][lda], B [N][ldb] fp32.
- * mode FPEPS_F32: CUDA-core FP32; FPEPS_TF32X3: tensor-core 3xTF32 (needs
- * M, N >= 128, K >= 32, lda and ldb multiples of 4, 16-byte aligned A and B,
- * else FPEPS_ERR_UNSUPPORTED). Synchronises `cuda_stream` for TF32X3. */
+ * mode FPEPS_F32: CUDA-core FP32; FPEPS_TF32X3 / FPEPS_BF16X3: tensor-core
+ * 3xTF32 / 3xBF16 (needs K >= 32, lda and ldb multiples of 4, 16-byte aligned
+ * A and B, else FPEPS_ERR_UNSUPPORTED). Synchronises `cuda_stream` for the
+ * tensor-core modes. */
 fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                             const float* B, int64_t ldb, float* C, void* cuda_stream);
 

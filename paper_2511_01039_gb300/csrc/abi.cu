@@ -236,7 +236,6 @@ fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, con
   if (c.n_envs != 1) return FPEPS_ERR_UNSUPPORTED;
   if (c.symmetry != 0 && c.symmetry != 1) return FPEPS_ERR_ARG;
   if ((c.symmetry == 1) != (charges_host != nullptr)) return FPEPS_ERR_ARG;
-  if (c.prec == FPEPS_BF16X3) return FPEPS_ERR_UNSUPPORTED;   // 3xBF16 kernels are not built
   fpeps_env* env = new (std::nothrow) fpeps_env();
   if (!env) return FPEPS_ERR_OOM;
   env->cfg = c;
@@ -582,7 +581,7 @@ fpeps_status fpeps_gemm_f32(int32_t mode, int64_t M, int64_t N, int64_t K, const
       fpeps::gemm_simt<float>(s, M, N, K, 1.0f, A, lda, 1, B, ldb, 1, 0.0f, C, om);
       return;
     }
-    if (mode != FPEPS_TF32X3) throw Error{FPEPS_ERR_UNSUPPORTED, "mode"};
+    if (mode != FPEPS_TF32X3 && mode != FPEPS_BF16X3) throw Error{FPEPS_ERR_UNSUPPORTED, "mode"};
     if (!fpeps::gemm_tc_supported(M, N, K, lda, ldb) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16))
       throw Error{FPEPS_ERR_UNSUPPORTED, "shape not supported by the tensor-core kernel"};
     const size_t sb = fpeps::gemm_tc_scratch_bytes(mode, M, N, K);

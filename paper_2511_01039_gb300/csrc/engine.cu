@@ -242,7 +242,7 @@ struct Engine : EngineBase {
                 int how = TALL_PLAIN) {
     const int kp = (k + 3) & ~3;
     if (how == TALL_CALIBRATED && n <= kCalCols) how = TALL_CUDA_CORES;
-    if (sizeof(T) == 4 && mode == FPEPS_TF32X3 && how != TALL_CUDA_CORES && !simt_only &&
+    if (sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && how != TALL_CUDA_CORES && !simt_only &&
         gemm_tc_supported(m, n, k, kp, kp)) {
       Arena ar = arena();
       T* Xt = ar.get_n<T>((size_t)m * kp);
@@ -284,7 +284,7 @@ struct Engine : EngineBase {
     P.n = n;
     P.a = a;
     P.ap = (a + 3) & ~3;
-    P.tc = sizeof(T) == 4 && mode == FPEPS_TF32X3 && a >= 1 && gemm_tc_supported(a, 1, n, n, n) &&
+    P.tc = sizeof(T) == 4 && (mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3) && a >= 1 && gemm_tc_supported(a, 1, n, n, n) &&
            gemm_tc_supported(n, 1, P.ap, P.ap, P.ap) && ((uintptr_t)Vm % 16) == 0;
     if (P.tc) {
       P.VmT = ar.get_n<T>((size_t)n * P.ap);

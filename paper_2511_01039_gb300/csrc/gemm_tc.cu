@@ -56,7 +56,7 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128, BN = 128, BK = 32;   // BK fp32 = 128 bytes = one 128B swizzle row
-constexpr int TILE_A = BM * BK * 4, TILE_B = BN * BK * 4;       // bytes
+constexpr int TILE_A = BM * BK * 4;   // bytes
 constexpr int EPI_TILE = 32 * 33;                                 // floats: one warp's 32x32 output block
 struct TcArgs {
   int64_t M, N, K;
@@ -129,7 +129,10 @@ __device__ __forceinline__ bool handoff_abort(bool mine) {
   return r != 0;
 }
 
-template <bool PAIR>
+// BF: the BF16x3 form (kind::f16 MMAs with BF16 hi/lo splits, K = 16 per MMA): A's hi/lo slots
+// are half as wide (two BF16 per TMEM column), B's BF16 hi/lo go to a no-swizzle K-major image
+// beside the landed FP32 tile, and a k-block takes 6 MMAs instead of 12.
+template <bool PAIR, bool BF>
 __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_constant__ CUtensorMap mapA,
                                                                 const __grid_constant__ CUtensorMap mapB, TcArgs g) {
   // CTA pair (cluster of two): each CTA holds 128 rows of a 256-row tile (A in its
@@ -178,6 +181,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
   auto A_f = [&](int st) { return smem + st * T_STAGE_BYTES; };
   auto B_hi = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A; };
   auto B_lo = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A + TILE_BH; };
+  // BF16 images of B (BF): hi then lo, element (n, k) at (k / 8) LB + (n / 8) 128 + (n % 8) 16 + (k % 8) 2
+  constexpr uint32_t LB = (uint32_t)(BNH / 8) * 128;   // K-direction core-matrix stride of a BF16 image
+  auto B_h16 = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A + TILE_BH; };
+  auto B_l16 = [&](int st) { return smem + st * T_STAGE_BYTES + TILE_A + TILE_BH + TILE_BH / 2; };
+  constexpr uint32_t AW = BF ? 32 : 64;                 // TMEM columns of an A slot (hi, then lo)
   auto tile_mn = [&](int64_t tile, int64_t& m0, int64_t& n0) {
     tile %= g.mt * g.nt;
     const int64_t mt = g.m_fast ? tile % g.mt : tile / g.nt;
@@ -249,8 +257,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
     // drained (measured: one wait per 12 MMAs halves the tensor-pipe rate). The
     // waiter warp does the mbarrier waits and hands each ready k-block over on a
     // named barrier, whose OR-reduction also carries an abort.
-    const uint32_t idesc =
-        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BNT >> 3) << 17) | ((uint32_t)((BM * CS) >> 4) << 24);
+    // D FP32; A, B TF32 (2) or BF16 (1); N; M
+    const uint32_t idesc = (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) |
+                           ((uint32_t)(BNT >> 3) << 17) | ((uint32_t)((BM * CS) >> 4) << 24);
     int it = 0, lc = 0;
     bool ok = true;
     for (int64_t tile = tile0; tile < ntiles && ok; tile += tstep) {
@@ -265,14 +274,26 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int st = it % T_STAGES, as = PAIR ? it % NSLOT : st;
           if (lane == 0) {
-            const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
-            const uint32_t ah = tmem + abase + (uint32_t)(as * 64), al = ah + 32;
+            const uint32_t ah = tmem + abase + (uint32_t)(as * AW), al = ah + AW / 2;
+            if constexpr (BF) {
+              const uint8_t* bh = B_h16(st);
+              const uint8_t* bl = B_l16(st);
 #pragma unroll
-            for (int kk = 0; kk < BK / 8; ++kk) {
-              const uint64_t o = (uint64_t)(kk * 32) >> 4;
-              mma_tf32_ts<PAIR>(d, al + (uint32_t)(kk * 8), bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
-              mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
-              mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
+              for (int kk = 0; kk < BK / 16; ++kk) {   // K = 16 per MMA: two core-matrix columns
+                const uint64_t dh = sdesc_noswz(bh + 2 * kk * LB, LB, 128), dl = sdesc_noswz(bl + 2 * kk * LB, LB, 128);
+                mma_bf16_ts<PAIR>(d, al + (uint32_t)(kk * 8), dh, idesc, ((kb - c0) | kk) ? 1u : 0u);
+                mma_bf16_ts<PAIR>(d, ah + (uint32_t)(kk * 8), dl, idesc, 1u);
+                mma_bf16_ts<PAIR>(d, ah + (uint32_t)(kk * 8), dh, idesc, 1u);
+              }
+            } else {
+              const uint64_t bh = sdesc(B_hi(st)), bl = sdesc(B_lo(st));
+#pragma unroll
+              for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                mma_tf32_ts<PAIR>(d, al + (uint32_t)(kk * 8), bh + o, idesc, ((kb - c0) | kk) ? 1u : 0u);
+                mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bl + o, idesc, 1u);
+                mma_tf32_ts<PAIR>(d, ah + (uint32_t)(kk * 8), bh + o, idesc, 1u);
+              }
             }
             mma_commit<PAIR>(&empty[st], (1u << CS) - 1);   // frees the stage (both CTAs) ...
             if constexpr (PAIR) mma_commit<PAIR>(&aempty[as], (1u << CS) - 1);   // ... and the A slot
@@ -339,6 +360,31 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint4* row = (const uint4*)(A_f(st) + r * 128);
+        if constexpr (BF) {
+          // two BF16 per TMEM column (the lower K index in the lower half)
+          uint32_t h2[16], l2[16];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint4 v = row[c ^ (r & 7)];   // 128-byte swizzle: chunk c of row r
+            uint32_t h[4], l[4];
+            bf16_split(__uint_as_float(v.x), h[0], l[0]);
+            bf16_split(__uint_as_float(v.y), h[1], l[1]);
+            bf16_split(__uint_as_float(v.z), h[2], l[2]);
+            bf16_split(__uint_as_float(v.w), h[3], l[3]);
+            h2[2 * c] = h[0] | (h[1] << 16);
+            h2[2 * c + 1] = h[2] | (h[3] << 16);
+            l2[2 * c] = l[0] | (l[1] << 16);
+            l2[2 * c + 1] = l[2] | (l[3] << 16);
+          }
+          const uint32_t ta = tmem + lane_base + abase + (uint32_t)(as * AW);
+          tmem_st16(ta, h2);
+          tmem_st16(ta + AW / 2, l2);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive_issuer<PAIR>(&aconv[as], rank);
+          continue;
+        }
         float hi[32], lo[32];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -351,7 +397,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             lo[c * 4 + e] = __uint_as_float(tf32_round(__float_as_uint(__uint_as_float(w[e]) - __uint_as_float(h))));
           }
         }
-        const uint32_t ta = tmem + lane_base + abase + (uint32_t)(as * 64);
+        const uint32_t ta = tmem + lane_base + abase + (uint32_t)(as * AW);
         tmem_st32(ta, hi);
         tmem_st32(ta + 32, lo);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -373,6 +419,34 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int st = it % T_STAGES;
         if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
+        if constexpr (BF) {
+          // the landed FP32 tile (128-byte swizzle) -> BF16 hi and lo images, 4 elements per step
+          const uint4* src = (const uint4*)B_hi(st);
+          uint8_t* h16 = B_h16(st);
+          uint8_t* l16 = B_l16(st);
+          for (int e = cw * 32 + lane; e < TILE_BH / 32; e += NBW * 32) {
+            // row n, 8-element group j (k = 8j .. 8j+7). Lanes walk rows: a quarter warp reads eight
+            // distinct 16-byte columns of the swizzled tile and writes 128 contiguous bytes
+            const int n = e % BNH, j = e / BNH;
+            const uint4 v0 = src[n * 8 + ((2 * j) ^ (n & 7))];
+            const uint4 v1 = src[n * 8 + ((2 * j + 1) ^ (n & 7))];
+            const float f[8] = {__uint_as_float(v0.x), __uint_as_float(v0.y), __uint_as_float(v0.z),
+                                __uint_as_float(v0.w), __uint_as_float(v1.x), __uint_as_float(v1.y),
+                                __uint_as_float(v1.z), __uint_as_float(v1.w)};
+            uint32_t h[8], l[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) bf16_split(f[q], h[q], l[q]);
+            const uint32_t off = (uint32_t)j * LB + (uint32_t)(n / 8) * 128 + (uint32_t)(n % 8) * 16;
+            *(uint4*)(h16 + off) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16),
+                                              h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+            *(uint4*)(l16 + off) = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16),
+                                              l[4] | (l[5] << 16), l[6] | (l[7] << 16));
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive_issuer<PAIR>(&bconv[st], rank);
+          continue;
+        }
         uint4* bh = (uint4*)B_hi(st);
         uint4* blo = (uint4*)B_lo(st);
 #pragma unroll 3
@@ -594,7 +668,9 @@ static int sm_count() {
 static int pair_slots() {
   static int n = -1;
   if (n < 0) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 t_smem_bytes<true>()));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  t_smem_bytes<true>()));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(sm_count() & ~1));
@@ -608,7 +684,7 @@ static int pair_slots() {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int c = 0;
-    if (cudaOccupancyMaxActiveClusters(&c, k_gemm_tf32x3_t<true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&c, k_gemm_tf32x3_t<true, false>, &cfg) != cudaSuccess) {
       (void)cudaGetLastError();
       c = 0;
     }
@@ -645,12 +721,15 @@ size_t gemm_tc_scratch_bytes(int, int64_t M, int64_t N, int64_t K) {
 
 void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
              int64_t ldb, float* C, OutMap om, void* scratch, size_t scratch_bytes, bool hold_loads) {
-  FP_CHECK(mode == FPEPS_TF32X3, FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: only 3xTF32 is built");
+  FP_CHECK(mode == FPEPS_TF32X3 || mode == FPEPS_BF16X3, FPEPS_ERR_UNSUPPORTED, "tensor-core GEMM: 3xTF32 or 3xBF16");
+  const bool bf = mode == FPEPS_BF16X3;
   FP_CHECK(scratch && scratch_bytes >= sizeof(int), FPEPS_ERR_ARG, "tensor-core GEMM: scratch");
   FP_CHECK(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, FPEPS_ERR_ARG, "tensor-core GEMM: operand alignment");
   static bool attr = false;
   if (!attr) {
-    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 t_smem_bytes<false>()));
+    FP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_t<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  t_smem_bytes<false>()));
     attr = true;
   }
@@ -688,10 +767,12 @@ void gemm_tc(cudaStream_t s, int mode, int64_t M, int64_t N, int64_t K, const fl
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    FP_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_tf32x3_t<true>, ma, mb, g));
+    if (bf) FP_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_tf32x3_t<true, true>, ma, mb, g));
+    else FP_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_tf32x3_t<true, false>, ma, mb, g));
   } else {
-    k_gemm_tf32x3_t<false><<<(unsigned)std::min<int64_t>(tiles, p.slots), P_THREADS, t_smem_bytes<false>(), s>>>(ma, mb,
-                                                                                                             g);
+    const unsigned grid1 = (unsigned)std::min<int64_t>(tiles, p.slots);
+    if (bf) k_gemm_tf32x3_t<false, true><<<grid1, P_THREADS, t_smem_bytes<false>(), s>>>(ma, mb, g);
+    else k_gemm_tf32x3_t<false, false><<<grid1, P_THREADS, t_smem_bytes<false>(), s>>>(ma, mb, g);
   }
   FP_LAUNCH();
   if (g.nsplit > 1) {

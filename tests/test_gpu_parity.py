@@ -193,7 +193,9 @@ def test_product_state_closed_form_on_gpu(fp):
     # subspace; the deviation is bounded by the truncation error (~1% here), not by FP32
     (False, "f32", 2e-2), (False, "tf32x3", 2e-2),
     # separated spectra: FP32-class agreement
-    (True, "f64", 1e-8), (True, "f32", 1e-5), (True, "tf32x3", 1e-5 * TF32X3_OVER_F32)])
+    (True, "f64", 1e-8), (True, "f32", 1e-5), (True, "tf32x3", 1e-5 * TF32X3_OVER_F32),
+    # 3xBF16 (boundary and environment GEMMs): 3 * 2^-16 per product, 64x the 3xTF32 bound
+    (False, "bf16x3", 2e-2), (True, "bf16x3", 1e-5 * TF32X3_OVER_F32 * 64)])
 def test_c2_against_stored_oracle(fp, decay, prec, tol):
     """4x4, D=4, w=4, chi=64 truncated; oracle values written by tests/golden/make_golden.py."""
     path = os.path.join(HERE, "golden", "c2_fsm_decay_seed0.json" if decay else "c2_fsm_seed0.json")
