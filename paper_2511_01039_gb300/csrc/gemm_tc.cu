@@ -349,15 +349,20 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
       for (int kb = 0; kb < nk; ++kb, ++it) {
         if (NAS > 1 && it % NAS != set) continue;
         const int st = it % T_STAGES, as = PAIR ? it % NSLOT : st;
-        if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
         // the slot is free once the MMAs of its previous k-block are done. Single CTA: the
         // slot is the stage's, and the TMA refill of the stage waited for the same release,
-        // so this wait passes at once; pair CTA: the A-slot ring of its own (two back)
+        // so this wait passes at once; pair CTA: the A-slot ring of its own (two back).
+        // In a pair CTA a converter set sees a stage only every other fill when the ring
+        // length is odd, so a parity wait on full[st] alone could match the fill two back
+        // while the previous one is still landing. The slot wait comes first: once the MMAs
+        // of k-block it - 2 are done, the fill of it - T_STAGES has landed (those MMAs
+        // consumed it), so full[st] is in the phase of k-block it and the parity is exact.
         if (PAIR ? !mbar_wait(&aempty[as], ((it / NSLOT) & 1) ^ 1, abort_flag)
                  : !mbar_wait(&empty[st], ((it / T_STAGES) & 1) ^ 1, abort_flag)) {
           ok = false;
           break;
         }
+        if (!mbar_wait(&full[st], (it / T_STAGES) & 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint4* row = (const uint4*)(A_f(st) + r * 128);
         if constexpr (BF) {

@@ -290,13 +290,15 @@ def _spec_err(got, ref):
 
 
 @pytest.mark.skipif(not os.path.exists(C3ROW), reason="stored C3 row not written (tests/golden/make_golden.py --c3row)")
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 1e-4), ("tf32x3", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("f32", 5e-5), ("tf32x3", 5e-5), ("bf16x3", 1e-4)])
 def test_c3_row2_against_stored_oracle(fp, prec, tol):
     """6x6, D=6, w=4 (Hubbard-shaped FSM), chi=256: row 2 absorbed into a seeded boundary MPS by
     the zip-up rSVD and one CBE fit pass (Sec. IV), against the FP64 oracle's stored result:
     the row's log-scale and the kept spectrum of every bond after the zip-up and after the fit.
-    FP64 must agree to 1e-8; the FP32 and 3xTF32 paths are held to 1e-4 (FP32 rounding amplified
-    through the chained factorisations of one row)."""
+    FP64 must agree to 1e-8. Measured: FP32 6e-8 / 3.5e-7 / up to 1.1e-5 (log-scale, zip, fit),
+    3xTF32 1.5e-6 / 5.3e-6 / 4.7e-6, 3xBF16 3.3e-6 / 3.5e-6 / 2.5e-5; the bounds leave a factor
+    of four or more (the fit is a variational step whose result moves with every rounding of
+    the zip-up it starts from)."""
     gold, ls, zs, fs = _c3_row2(fp, prec)
     errs = {"log_scale": abs(ls - gold["log_scale"]),
             "zip": max(_spec_err(z, r) for z, r in zip(zs, gold["zip_spectra"])),
@@ -305,3 +307,17 @@ def test_c3_row2_against_stored_oracle(fp, prec, tol):
     assert errs["log_scale"] < tol
     assert errs["zip"] < tol
     assert errs["fit"] < tol
+
+
+@pytest.mark.skipif(not os.path.exists(C3ROW), reason="stored C3 row not written (tests/golden/make_golden.py --c3row)")
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_c3_row2_repeatable(fp, prec):
+    """The same C3 row twice on the tensor-core path: the results agree to the level of
+    floating-point reordering (FP64 atomics in the reductions), ~1e-8 on the log-scale. A pair
+    GEMM whose converters read a stage before its fill has landed gave run-to-run differences
+    of 1e-4 here."""
+    _, ls1, zs1, fs1 = _c3_row2(fp, prec)
+    _, ls2, zs2, fs2 = _c3_row2(fp, prec)
+    assert abs(ls1 - ls2) < 1e-7
+    assert max(_spec_err(a, b) for a, b in zip(zs1, zs2)) < 1e-6
+    assert max(_spec_err(a, b) for a, b in zip(fs1, fs2)) < 1e-5
