@@ -171,10 +171,11 @@ def cpu_sample(seconds: float, workload):
 
 # ----------------------------------------------------------------------------- ranks
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of a
-# kernel class, from one ncu capture of the probe case each (bench.py --probe-theta 8: both
-# GEMM launches; one k_sandwich_tc launch); traffic per launch = ratio x the algorithmic
-# bytes of an average launch (traffic grows with the bytes moved)
-DRAM_PER_ALG_BYTE = {"gemm_tc_tf32x3": (0.911 + 1.020) / (2 * 0.966), "sandwich": (0.675 + 0.689) / 1.493}
+# kernel class, from one ncu capture of the probe case each (bench.py --probe-theta 8: the
+# environment x vectors GEMM launch, 0.966 GB algorithmic; one k_sandwich_tc launch, 1.493 GB);
+# traffic per launch = ratio x the algorithmic bytes of an average launch (traffic grows with
+# the bytes moved)
+DRAM_PER_ALG_BYTE = {"gemm_tc_tf32x3": (0.9632 + 0.0036) / 0.966, "sandwich": (0.649 + 0.689) / 1.493}
 
 
 def roofline_of(kind: str, d: dict, prec: str, peaks: dict) -> dict:

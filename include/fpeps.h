@@ -233,6 +233,27 @@ fpeps_status fpeps_bond_spectrum(const fpeps_env* env, int32_t which, int32_t c,
 fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void* el_host, int32_t k,
                                const void* x_host, void* y_host);
 
+/* The four site maps of the staged row on k host vectors (Sec. IV: the rSVD
+ * applies the site matrix and its transpose; the CBE fit of Sec. IV / Fig. 5
+ * applies the same contraction pattern 2(a) of Sec. III with the environment
+ * on the right). Notation: t = left bond of the boundary tensor T_c, t' = its
+ * right bond, L, R, Dn = the (ket, PEPO, bra) bundles of the site's left,
+ * right and down legs, a = the caller's environment bond. All host arrays are
+ * C order, vector index outermost, bundles in (ket, PEPO, bra) order:
+ *   op 0  Y = Theta_c X          env [a][t][L]   in X [k][t'][R]  out Y [k][a][Dn]
+ *   op 1  Z = Theta_c^T Y        env [a][t][L]   in Y [k][a][Dn]  out Z [k][t'][R]
+ *   op 2  Z = ThetaR_c X         env [a][t'][R]  in X [k][Dn][a]  out Z [k][t][L]
+ *   op 3  X = ThetaR_c^T Z       env [a][t'][R]  in Z [k][t][L]   out X [k][Dn][a]
+ * where ThetaR_c maps a vector on (Dn, a) through the right environment, the
+ * site sandwich and T_c to (t, L). The buffers are the caller's and must hold
+ * the sizes above (the library cannot check host sizes). Element type =
+ * compute precision; the products run in the env's precision mode on the same
+ * kernels as the compress step. Synchronises the stream.
+ * Errors: FPEPS_ERR_ARG for op outside 0..3, c outside the row, a, k < 1 or a
+ * NULL buffer; FPEPS_ERR_STATE when no row is staged. */
+fpeps_status fpeps_apply_theta_op(fpeps_env* env, int32_t op, int32_t c, int32_t a, const void* env_host, int32_t k,
+                                  const void* in_host, void* out_host);
+
 /* One contraction GEMM of the path on caller device buffers (diagnostic):
  * C[M][N] (row-major) = sum_k A[m][k] B[n][k]; A [M][lda], B [N][ldb] fp32.
  * mode FPEPS_F32: CUDA-core FP32; FPEPS_TF32X3 / FPEPS_BF16X3: tensor-core

@@ -535,7 +535,18 @@ fpeps_status fpeps_apply_theta(fpeps_env* env, int32_t c, int32_t a, const void*
     if (env->state != fpeps::RowState::Staged) throw Error{FPEPS_ERR_STATE, "no staged row"};
     if (c < 0 || c >= env->cfg.Ly || a < 1 || k < 1 || !el_host || !x_host || !y_host)
       throw Error{FPEPS_ERR_ARG, "bad argument"};
-    env->engine->apply_theta_host(env, c, a, el_host, k, x_host, y_host);
+    env->engine->apply_theta_host(env, 0, c, a, el_host, k, x_host, y_host);
+  });
+}
+
+fpeps_status fpeps_apply_theta_op(fpeps_env* env, int32_t op, int32_t c, int32_t a, const void* env_host, int32_t k,
+                                  const void* in_host, void* out_host) {
+  return fpeps::guard(env, [&] {
+    fpeps::check_env(env);
+    if (op < 0 || op > 3 || c < 0 || c >= env->cfg.Ly || a < 1 || k < 1 || !env_host || !in_host || !out_host)
+      throw Error{FPEPS_ERR_ARG, "bad argument"};
+    if (env->state != fpeps::RowState::Staged) throw Error{FPEPS_ERR_STATE, "no staged row"};
+    env->engine->apply_theta_host(env, op, c, a, env_host, k, in_host, out_host);
   });
 }
 

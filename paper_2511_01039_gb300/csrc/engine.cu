@@ -1650,33 +1650,53 @@ struct Engine : EngineBase {
   }
 
   // ---------------------------------------------------------------- diagnostics
-  void apply_theta_host(fpeps_env* e, int c, int a, const void* el, int k, const void* x, void* y) override {
+  // one site map of the staged row on host vectors (layouts in include/fpeps.h,
+  // fpeps_apply_theta_op): the host arrays are brought to the layouts of theta,
+  // theta_t, theta_r and theta_r_t, and the results back
+  void apply_theta_host(fpeps_env* e, int op, int c, int a, const void* envh, int k, const void* in,
+                        void* out) override {
     const int row = e->staged_row;
     FP_CHECK(row > 0, FPEPS_ERR_STATE, "no staged row");
     ensure_sandwich(e, e->layer, row);
     Arena ar = arena();
-    Site st = make_site(ar, row, c, true, false);
+    const bool right = op >= 2;
+    Site st = make_site(ar, row, c, !right, right);
     const int64_t t = st.t, L = st.bL, tp = st.tp, R = st.bR, Dn = st.bD;
-    // el [a][t][L]; x [k][t'][R]; y [k][a][Dn]  (host, C order)
-    T* elv = ar.get_n<T>((int64_t)a * t * L);
-    FP_CUDA(cudaMemcpyAsync(elv, el, sizeof(T) * a * t * L, cudaMemcpyHostToDevice, s));
+    // environment: [a][t][L] (left) or [a][t'][R] (right); E bundle PEPO-outermost, Et [bond][bundle][a]
+    const int64_t bond = right ? tp : t, bun = right ? R : L;
+    T* ev = ar.get_n<T>((int64_t)a * bond * bun);
+    FP_CUDA(cudaMemcpyAsync(ev, envh, sizeof(T) * a * bond * bun, cudaMemcpyHostToDevice, s));
     Env3 E;
     E.a = a;
-    T* elo = ar.get_n<T>((int64_t)a * t * L);   // L PEPO-outermost (see env_from_vectors)
-    bundle_outer<T>(s, elv, elo, (int64_t)a * t, st.nA[0], st.nW[0]);
-    E.E = elo;
-    T* Et = ar.get_n<T>((int64_t)a * t * L);
-    permute3<T>(s, elv, Et, a, t, L, 1, 2, 0);
-    E.Et = Et;
-    T* xh = ar.get_n<T>((int64_t)k * tp * R);
-    FP_CUDA(cudaMemcpyAsync(xh, x, sizeof(T) * k * tp * R, cudaMemcpyHostToDevice, s));
-    T* X = ar.get_n<T>((int64_t)k * tp * R);
-    permute3<T>(s, xh, X, k, tp, R, 0, 2, 1);
-    T* Y = ar.get_n<T>((int64_t)k * Dn * a);
-    theta(st, E, X, Y, k);
-    T* yh = ar.get_n<T>((int64_t)k * Dn * a);
-    permute3<T>(s, Y, yh, k, Dn, a, 0, 2, 1);
-    FP_CUDA(cudaMemcpyAsync(y, yh, sizeof(T) * k * Dn * a, cudaMemcpyDeviceToHost, s));
+    T* eo = ar.get_n<T>((int64_t)a * bond * bun);
+    bundle_outer<T>(s, ev, eo, (int64_t)a * bond, st.nA[right ? 2 : 0], st.nW[right ? 2 : 0]);
+    E.E = eo;
+    T* et = ar.get_n<T>((int64_t)a * bond * bun);
+    permute3<T>(s, ev, et, a, bond, bun, 1, 2, 0);
+    E.Et = et;
+    // sizes of the input and output per vector, and the host-side index pair to swap (0: none)
+    int64_t n_in = 0, n_out = 0, in_d1 = 0, in_d2 = 0, out_d1 = 0, out_d2 = 0;
+    switch (op) {
+      case 0: n_in = tp * R; n_out = a * Dn; in_d1 = tp; in_d2 = R; out_d1 = Dn; out_d2 = a; break;
+      case 1: n_in = a * Dn; n_out = tp * R; in_d1 = a; in_d2 = Dn; out_d1 = R; out_d2 = tp; break;
+      case 2: n_in = Dn * a; n_out = t * L; out_d1 = L; out_d2 = t; break;
+      default: n_in = t * L; n_out = Dn * a; in_d1 = t; in_d2 = L; break;
+    }
+    T* ih = ar.get_n<T>((int64_t)k * n_in);
+    FP_CUDA(cudaMemcpyAsync(ih, in, sizeof(T) * k * n_in, cudaMemcpyHostToDevice, s));
+    T* X = ih;
+    if (in_d1) {
+      X = ar.get_n<T>((int64_t)k * n_in);
+      permute3<T>(s, ih, X, k, in_d1, in_d2, 0, 2, 1);
+    }
+    T* Y = ar.get_n<T>((int64_t)k * n_out);
+    run_op(op, st, E, X, Y, k);
+    T* oh = Y;
+    if (out_d1) {
+      oh = ar.get_n<T>((int64_t)k * n_out);
+      permute3<T>(s, Y, oh, k, out_d1, out_d2, 0, 2, 1);
+    }
+    FP_CUDA(cudaMemcpyAsync(out, oh, sizeof(T) * k * n_out, cudaMemcpyDeviceToHost, s));
     FP_CUDA(cudaStreamSynchronize(s));
   }
 };

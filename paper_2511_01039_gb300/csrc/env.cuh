@@ -81,7 +81,8 @@ struct EngineBase {
   virtual void first_row(fpeps_env* env, int row) = 0;
   virtual void close_row(fpeps_env* env, int row) = 0;
   virtual void compress(fpeps_env* env, int row, const fpeps_rsvd_params& prm, fpeps_stats* st) = 0;
-  virtual void apply_theta_host(fpeps_env* env, int c, int a, const void* el, int k, const void* x, void* y) = 0;
+  virtual void apply_theta_host(fpeps_env* env, int op, int c, int a, const void* envh, int k, const void* in,
+                                void* out) = 0;
 };
 
 EngineBase* make_engine(fpeps_env* env);

@@ -74,6 +74,8 @@ SIGNATURES = {
                                       C.POINTER(C.c_int32)]),
     "fpeps_apply_theta": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                                     C.c_void_p]),
+    "fpeps_apply_theta_op": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
+                                       C.c_void_p, C.c_void_p]),
     "fpeps_gemm_f32": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.c_int64, C.c_void_p, C.c_void_p]),
     "fpeps_svd_f64": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -227,6 +229,20 @@ def fpeps_apply_theta(env, c: int, el, x, dn: int, elem_bytes: int):
     return y
 
 
+def fpeps_apply_theta_op(env, op: int, c: int, envt, x, out_shape, elem_bytes: int):
+    """Site map `op` of the staged row (0: Theta, 1: Theta^T, 2: ThetaR, 3: ThetaR^T) on host
+    vectors x [k, ...] with the environment envt [a, bond, bundle]; returns out [k, *out_shape]."""
+    import numpy as np
+    dt = np.float64 if elem_bytes == 8 else np.float32
+    envt = np.ascontiguousarray(envt, dtype=dt)
+    x = np.ascontiguousarray(x, dtype=dt)
+    k = x.shape[0]
+    y = np.zeros((k,) + tuple(out_shape), dtype=dt)
+    _check(env, lib().fpeps_apply_theta_op(env, op, c, envt.shape[0], envt.ctypes.data, k, x.ctypes.data,
+                                           y.ctypes.data))
+    return y
+
+
 def fpeps_gemm_f32(mode: int, A, B, C, K=None, stream_handle: int = 0):
     """C = A[:, :K] @ B[:, :K].T for torch CUDA float32 tensors (unit inner stride); C [M,N] contiguous."""
     M = A.shape[0]
@@ -335,6 +351,10 @@ class Env:
     def apply_theta(self, c, el, x, dn):
         """One Theta_c application of the staged row (diagnostic): el [a,t,L], x [k,t',R] -> y [k,a,dn]."""
         return fpeps_apply_theta(self.h, c, el, x, dn, self.elem)
+
+    def apply_theta_op(self, op, c, envt, x, out_shape):
+        """One site map of the staged row (diagnostic; layouts of fpeps_apply_theta_op)."""
+        return fpeps_apply_theta_op(self.h, op, c, envt, x, out_shape, self.elem)
 
 
 def pack_charges(qpeps, qpepo=None):

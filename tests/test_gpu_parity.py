@@ -116,6 +116,49 @@ def test_apply_theta_small_sites(fp, prec, tol):
     env.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 1e-5), ("tf32x3", 1e-5), ("bf16x3", 1e-4)])
+def test_site_maps_all_ops_against_oracle(fp, prec, tol):
+    """The four site maps of an interior row (Theta, Theta^T, and the right-environment map and its
+    transpose of the fit) on every site, element by element against the oracle's theta, theta_t,
+    theta_r and theta_r_t; and the adjoint identities <Y, Theta X> = <Theta^T Y, X>,
+    <Z, ThetaR X> = <ThetaR^T Z, X> on the GPU results. D=5 with chi=150 puts the environment
+    products (K = t * |L| up to 150 * 100) on the tensor cores in the split modes."""
+    peps = L.random_peps(4, 4, 5, 4, seed=21)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=21))
+    T, _ = B.first_row_boundary(peps[0], pepo[0])
+    env = _env(fp, peps, pepo, D=5, w=4, chi=150, prec=prec, seed=5)
+    fp.fpeps_absorb_row(env.h, 0, 1)
+    fp.fpeps_absorb_row(env.h, 1, 1)
+    g = np.random.default_rng(3)
+    for c in range(4):
+        A, W = peps[1][c], pepo[1][c]
+        t, tp = T[c].shape[0], T[c].shape[2]
+        dL, dR, dD = B.bdim(A, W, 0), B.bdim(A, W, 2), B.bdim(A, W, 3)
+        a, k = 9, 6
+        el = g.standard_normal((a, t, dL))
+        er = g.standard_normal((a, tp, dR))
+        x0 = g.standard_normal((k, tp, dR))
+        y1 = g.standard_normal((k, a, dD))
+        x2 = g.standard_normal((k, dD, a))
+        z3 = g.standard_normal((k, t, dL))
+        outs = [env.apply_theta_op(0, c, el, x0, (a, dD)), env.apply_theta_op(1, c, el, y1, (tp, dR)),
+                env.apply_theta_op(2, c, er, x2, (t, dL)), env.apply_theta_op(3, c, er, z3, (dD, a))]
+        col = lambda v: np.moveaxis(v, 0, -1)
+        refs = [B.theta(el, T[c], A, W, col(x0)), B.theta_t(el, T[c], A, W, col(y1)),
+                B.theta_r(er, T[c], A, W, col(x2)), B.theta_r_t(er, T[c], A, W, col(z3))]
+        for op, (o, r) in enumerate(zip(outs, refs)):
+            r = np.moveaxis(r, -1, 0)
+            assert o.shape == r.shape, (op, c)
+            assert np.abs(o - r).max() <= tol * np.abs(r).max(), (op, c)
+        # adjoint pairs on the GPU's own outputs (fresh vectors of the matching shapes)
+        ip = lambda u, v: float(np.sum(u.astype(np.float64) * v.astype(np.float64)))
+        lhs, rhs = ip(y1, outs[0]), ip(env.apply_theta_op(1, c, el, y1, (tp, dR)), x0)
+        assert abs(lhs - rhs) <= 10 * tol * (abs(lhs) + np.linalg.norm(y1) * np.linalg.norm(outs[0])), c
+        lhs, rhs = ip(z3, outs[2]), ip(env.apply_theta_op(3, c, er, z3, (dD, a)), x2)
+        assert abs(lhs - rhs) <= 10 * tol * (abs(lhs) + np.linalg.norm(z3) * np.linalg.norm(outs[2])), c
+    env.close()
+
+
 def test_zip_spectrum_and_apply_theta_match_oracle(fp):
     peps = L.random_peps(4, 4, 2, 4, seed=4)
     pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=4))
@@ -312,12 +355,12 @@ def test_c3_row2_against_stored_oracle(fp, prec, tol):
 @pytest.mark.skipif(not os.path.exists(C3ROW), reason="stored C3 row not written (tests/golden/make_golden.py --c3row)")
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
 def test_c3_row2_repeatable(fp, prec):
-    """The same C3 row twice on the tensor-core path: the results agree to the level of
-    floating-point reordering (FP64 atomics in the reductions), ~1e-8 on the log-scale. A pair
-    GEMM whose converters read a stage before its fill has landed gave run-to-run differences
-    of 1e-4 here."""
+    """The same C3 row twice in one process on the tensor-core path: the results agree to the
+    level of floating-point reordering (measured: up to 3e-7 on the log-scale, a tenth of the
+    path's error against FP64). A pair GEMM whose converters read a stage before its fill had
+    landed gave run-to-run differences of 1e-4 on the log-scale and 1e-3 on the fit spectra."""
     _, ls1, zs1, fs1 = _c3_row2(fp, prec)
     _, ls2, zs2, fs2 = _c3_row2(fp, prec)
-    assert abs(ls1 - ls2) < 1e-7
-    assert max(_spec_err(a, b) for a, b in zip(zs1, zs2)) < 1e-6
-    assert max(_spec_err(a, b) for a, b in zip(fs1, fs2)) < 1e-5
+    assert abs(ls1 - ls2) < 1e-6
+    assert max(_spec_err(a, b) for a, b in zip(zs1, zs2)) < 1e-5
+    assert max(_spec_err(a, b) for a, b in zip(fs1, fs2)) < 5e-5
