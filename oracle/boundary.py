@@ -47,7 +47,7 @@ class RsvdParams:
     oversample: int = 10
     power_iters: int = 2
     chi_tilde: int = 0          # 0 => ceil(chi / 10)
-    n_fit: int = 1              # 0 or 1 right-to-left CBE fit passes
+    n_fit: int = 1              # right-to-left CBE fit passes (0: zip-up only)
     exact_svd: bool = False     # sketch width = full rank (exact factorisation)
 
 
@@ -303,7 +303,7 @@ def cbe_width(chi_t: int, rows_a: int, n_left: int, cols_a: int, n_right: int) -
 
 
 def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, layer: int, row: int,
-            env: int = 0, trace: list | None = None):
+            env: int = 0, trace: list | None = None, stage: int = 1):
     """Right-to-left variational fit with controlled bond expansion (Fig. 3-5).
 
     At each bond (c-1, c): V = row basis of the centre tensor at c; the
@@ -314,6 +314,7 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
 
     ``trace`` (test hook, no effect on the result): if a list is given, one dict
     per bond is appended with the inputs and outputs of the expansion step.
+    ``stage``: generator stage of the CBE sketch (pass p of the fit uses 1 + 16 (p - 1)).
     """
     Ly = len(T)
     chi_t = prm.chi_tilde if prm.chi_tilde > 0 else -(-chi // 10)
@@ -353,7 +354,7 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
         sa, vtil, k = np.zeros(0), np.zeros((0, cols_a)), 0
         if ct > 0:
             k = min(ct + prm.oversample, rows_a, cols_a)
-            omega = gaussian_sketch(cols_a, k, seed=seed, layer=layer, stage=1, site=c, row=row, env=env)
+            omega = gaussian_sketch(cols_a, k, seed=seed, layer=layer, stage=stage, site=c, row=row, env=env)
             _, _, sa, vt = rsvd(a_apply, a_apply_t, omega, prm.power_iters)
             vtil = (vt * live(sa)[:, None])[:ct]
             # the kept singular vectors lie in range(P_R^perp) unless A is (numerically)
@@ -387,15 +388,60 @@ def cbe_fit(T, Arow, Wrow, N, ELs, chi: int, prm: RsvdParams, *, seed: int, laye
     return out, rs_M + math.log(nrm), spectra
 
 
+def fit_stage(p: int) -> int:
+    """Generator stage of the CBE sketch of fit pass p = 1, 2, ... (stage 0 is the zip-up's
+    sketch, stage 2 the sign gauge's weights)."""
+    return 1 + 16 * (p - 1)
+
+
+def recanonicalize(T, Arow, Wrow, F):
+    """Left-to-right gauge sweep of a fitted boundary before another right-to-left
+    fit pass (Sec. IV: the fit of a bond needs the sites to its left in left-canonical
+    form, and the fit pass leaves them right-canonical).
+
+    F[0] is the unit-norm first tensor and F[c > 0] right isometries [a_{c-1}, Dn, a_c].
+    Each site, with the triangular factor of the site before it multiplied in, is
+    split by a thin QR; Q is the new left isometry and the factor moves right. The
+    left environment of the next site is the product of the rows above with the new
+    isometry, EL_{c+1} = (Theta_c^T N_c)^T (the same pattern 2(a) as the zip-up's
+    remainder), normalised by its Frobenius norm (the fit takes its scale from the
+    first site, whose environment is exactly 1). Returns (N, ELs) in the form the
+    zip-up returns them: N[c] left isometries for c < Ly-1, N[Ly-1] the unit-norm
+    last tensor, ELs[c] the left environment of site c.
+    """
+    Ly = len(F)
+    R = np.ones((1, 1))
+    EL = np.ones((1, 1, 1))
+    N, ELs = [], [EL]
+    for c in range(Ly - 1):
+        X = np.einsum("ab,bDc->aDc", R, F[c])
+        a1, dDn, ac = X.shape
+        Xm = X.reshape(a1 * dDn, ac)
+        Q = orth(Xm)
+        R = Q.T @ Xm                                      # X = Q R (Q spans the range of X)
+        Nc = Q.reshape(a1, dDn, ac)
+        N.append(Nc)
+        z = theta_t(EL, T[c], Arow[c], Wrow[c], Nc)       # [t', R, a_c]
+        el = np.moveaxis(z, -1, 0)
+        EL = el / np.linalg.norm(el)
+        ELs.append(EL)
+    X = np.einsum("ab,bDc->aDc", R, F[Ly - 1])
+    N.append(X / np.linalg.norm(X))
+    return N, ELs
+
+
 def absorb_row(T, Arow, Wrow, chi: int, prm: RsvdParams, *, seed: int, layer: int, row: int,
                env: int = 0) -> RowResult:
-    """One interior row: zip-up rSVD compression, then n_fit CBE fit passes."""
+    """One interior row: zip-up rSVD compression, then n_fit CBE fit passes (each pass
+    after the first starts from the previous one, re-canonicalised left to right)."""
     N, ELs, log_s, zsp = zipup(T, Arow, Wrow, chi, prm, seed=seed, layer=layer, row=row, env=env)
     if prm.n_fit == 0 or len(T) == 1:
         return RowResult(N, log_s, zsp, [])
-    if prm.n_fit != 1:
-        raise ValueError("n_fit must be 0 or 1")
     newT, log_f, fsp = cbe_fit(T, Arow, Wrow, N, ELs, chi, prm, seed=seed, layer=layer, row=row, env=env)
+    for p in range(2, prm.n_fit + 1):
+        N, ELs = recanonicalize(T, Arow, Wrow, newT)
+        newT, log_f, fsp = cbe_fit(T, Arow, Wrow, N, ELs, chi, prm, seed=seed, layer=layer, row=row, env=env,
+                                   stage=fit_stage(p))
     return RowResult(newT, log_f, zsp, fsp)
 
 

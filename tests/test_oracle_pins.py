@@ -109,7 +109,7 @@ def test_boundary_equals_brute_force_3x3(pepo_kind, chi):
     else:
         pepo = L.fsm_pepo(L.random_hamiltonian(3, 3, 4, 2, seed=1))
     num, _ = N.brute_force_expectation(peps, pepo)
-    for n_fit in (0, 1):
+    for n_fit in (0, 1, 2):
         prm = B.RsvdParams(exact_svd=True, n_fit=n_fit, power_iters=0)
         s, lv = B.contract(peps, pepo, chi, prm, seed=9, layer=1)
         assert _value(s, lv) == pytest.approx(num, rel=1e-10)
@@ -120,7 +120,7 @@ def test_boundary_untruncated_4x4_equals_columnwise():
     peps = L.random_peps(4, 4, 2, 4, seed=3)
     pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 0, seed=3))
     ex = N.exact_columnwise(peps, pepo)
-    for n_fit in (0, 1):
+    for n_fit in (0, 1, 2):
         s, lv = B.contract(peps, pepo, 64, B.RsvdParams(n_fit=n_fit), seed=1, layer=1)
         assert _value(s, lv) == pytest.approx(ex, rel=1e-10)
 
