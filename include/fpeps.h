@@ -84,11 +84,13 @@ typedef struct {
 
 /* rSVD / CBE settings (Sec. IV). Zero-initialised fields take the defaults in
  * brackets where stated. */
+#define FPEPS_MAX_FIT_PASSES 8
 typedef struct {
   int32_t oversample;   /* sketch width = kept bond + oversample            */
   int32_t power_iters;  /* q: applications of A^T A after the first A       */
   int32_t chi_tilde;    /* CBE expansion width; 0 => ceil(chi / 10)         */
-  int32_t n_fit;        /* 0 = zip-up only, 1 = zip-up + one CBE fit pass   */
+  int32_t n_fit;        /* CBE fit passes after the zip-up: 0 .. FPEPS_MAX_FIT_PASSES
+                           (more than 1: dense mode only, symmetry = 0)      */
   int32_t exact_svd;    /* 1 => sketch width = full rank (exact factorisation) */
 } fpeps_rsvd_params;
 
@@ -141,9 +143,15 @@ fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, con
 fpeps_status fpeps_absorb_row(fpeps_env* env, int32_t row, int32_t layer);
 
 /* Compress the staged row into a new boundary of bond chi: zip-up rSVD pass,
- * then n_fit CBE fit passes (Sec. IV). out_host (nullable) receives stats.
- * Errors: FPEPS_ERR_STATE if no interior row is staged, FPEPS_ERR_NUMERIC if a
- * factorisation broke down or a value became non-finite. */
+ * then n_fit CBE fit passes (Sec. IV, Fig. 3: the variational right-to-left fit
+ * with controlled bond expansion). Every pass after the first starts from the
+ * previous one re-canonicalised left to right (thin QR per site, the factor
+ * carried right, left environments rebuilt by pattern 2(a)); pass p draws its
+ * CBE sketch at generator stage 1 + 16 (p - 1). out_host (nullable) receives
+ * stats. Errors: FPEPS_ERR_STATE if no interior row is staged,
+ * FPEPS_ERR_NUMERIC if a factorisation broke down or a value became
+ * non-finite, FPEPS_ERR_UNSUPPORTED for n_fit outside 0 .. FPEPS_MAX_FIT_PASSES
+ * or n_fit > 1 with charge sectors. */
 fpeps_status fpeps_compress_rsvd(fpeps_env* env, const fpeps_rsvd_params* params, fpeps_stats* out_host);
 
 /* Value of the network closed by the last absorbed row (Sec. II: the energy

@@ -200,7 +200,7 @@ fpeps_rsvd_params norm_params(const fpeps_rsvd_params* p) {
   if (!p) throw Error{FPEPS_ERR_ARG, "params is NULL"};
   fpeps_rsvd_params q = *p;
   if (q.oversample < 0 || q.power_iters < 0 || q.chi_tilde < 0) throw Error{FPEPS_ERR_ARG, "negative rSVD parameter"};
-  if (q.n_fit < 0 || q.n_fit > 1) throw Error{FPEPS_ERR_UNSUPPORTED, "n_fit must be 0 or 1"};
+  if (q.n_fit < 0 || q.n_fit > FPEPS_MAX_FIT_PASSES) throw Error{FPEPS_ERR_UNSUPPORTED, "n_fit out of range"};
   return q;
 }
 

@@ -1069,13 +1069,28 @@ struct Engine : EngineBase {
         tb_new[c + 1] = b;
       }
     } else {
-      if (prm.n_fit != 1) throw Error{FPEPS_ERR_UNSUPPORTED, "n_fit must be 0 or 1"};
       if (sym) {
+        if (prm.n_fit != 1) throw Error{FPEPS_ERR_UNSUPPORTED, "charge sectors: n_fit must be 0 or 1"};
         std::vector<std::vector<int32_t>> qfit;
         log_row = fit_sym(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem, qnew, qfit);
         qnew = qfit;
       } else {
-        log_row = fit(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem);
+        log_row = fit(row, prm, Nvec, abond, EL, Nlast, T_new, tb_new, rowmem, 1);
+        // further passes start from the previous one, re-canonicalised left to right
+        for (int pass = 2; pass <= prm.n_fit; ++pass) {
+          Arena canon = arena();
+          std::vector<T*> Nv2(Ly, nullptr);
+          std::vector<int> ab2(Ly + 1, 1);
+          std::vector<Env3> EL2(Ly);
+          T* Nlast2 = nullptr;
+          recanonicalize(row, T_new, tb_new, canon, Nv2, ab2, EL2, Nlast2);
+          std::vector<void*> T_next(Ly, nullptr);
+          std::vector<int> tb_next(Ly + 1, 1);
+          log_row = fit(row, prm, Nv2, ab2, EL2, Nlast2, T_next, tb_next, canon, pass);
+          for (void* p : T_new) e->al.put(p);
+          T_new = T_next;
+          tb_new = tb_next;
+        }
       }
     }
     FP_CUDA(cudaStreamSynchronize(s));
@@ -1104,9 +1119,75 @@ struct Engine : EngineBase {
     }
   }
 
-  // Right-to-left variational fit with controlled bond expansion (Fig. 3-5).
+  // Left-to-right gauge sweep of a fitted boundary F (F[0] unit norm, F[c > 0] right isometries
+  // [a_{c-1}][Dn][a_c]) before another right-to-left fit pass, which needs the sites left of
+  // each bond left-canonical: each site, with the triangular factor of the one before it
+  // multiplied in, is split by a thin QR (Q the new left isometry, R carried right), and the
+  // left environment of the next site is EL_{c+1} = (Theta_c^T N_c)^T, pattern 2(a) as in the
+  // zip-up's remainder, normalised (the fit takes its scale from the first site, whose
+  // environment is exactly 1). Output in the zip-up's form: Nvec[c] vectors [a_c][Dn][a_{c-1}],
+  // abond, EL, and the unit-norm last tensor Nlast [a][Dn][1].
+  void recanonicalize(int row, const std::vector<void*>& F, const std::vector<int>& tb, Arena& mem,
+                      std::vector<T*>& Nvec, std::vector<int>& abond, std::vector<Env3>& EL, T*& Nlast) {
+    fpeps_env* e = env;
+    const int Ly = e->cfg.Ly;
+    EL[0] = unit_env(mem);
+    abond[0] = 1;
+    Arena rmem = arena();
+    T* Rt = nullptr;   // carried factor, a_in x a_in column-major (null: identity of size 1)
+    for (int c = 0; c < Ly; ++c) {
+      Arena ar = arena();
+      const int a_in = tb[c], a_out = tb[c + 1];
+      const int Dn = bund(e->sites[e->layer][row * Ly + c], 3);
+      const int64_t m = (int64_t)a_in * Dn;
+      // F_c [a_in][Dn][a_out] -> a_out vectors of (Dn, a_in), then X = R F_c on the a_in index
+      T* Fv = ar.get_n<T>(m * a_out);
+      permute3<T>(s, (const T*)F[c], Fv, a_in, Dn, a_out, 2, 1, 0);
+      T* X = Fv;
+      if (Rt) {
+        X = ar.get_n<T>(m * a_out);
+        mm(a_in, (int64_t)Dn * a_out, a_in, T(1), Rt, false, a_in, Fv, false, a_in, T(0), X, a_in);
+      }
+      if (c == Ly - 1) {   // the last tensor: X is [1][Dn][a] -> [a][Dn][1], unit norm
+        Nlast = mem.get_n<T>(m);
+        permute3<T>(s, X, Nlast, 1, Dn, a_in, 2, 1, 0);
+        const double nrm = host_norm(Nlast, m);
+        FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "re-canonicalisation: last tensor vanished");
+        scale_by_inv<T>(s, Nlast, m, e->d_scal);
+        abond[Ly - 1] = a_in;
+        break;
+      }
+      T* Q = mem.get_n<T>(m * a_out);
+      double* R = ar.get_n<double>((int64_t)a_out * a_out);
+      qr(X, m, a_out, Q, R);
+      Nvec[c] = Q;
+      abond[c + 1] = a_out;
+      // the factor for the next site (R row-major FP64 -> column-major copy)
+      Arena rnew = arena();
+      T* Rn = rnew.get_n<T>((int64_t)a_out * a_out);
+      convert_f64_t<T>(s, R, a_out, a_out, Rn);
+      rmem.reset();
+      rmem.live = rnew.live;
+      rnew.live.clear();
+      Rt = Rn;
+      // EL_{c+1}: Theta_c^T on the a_out columns of the isometry -> vectors [a_out][R][t']
+      Site st = make_site(ar, row, c, true, false);
+      const int64_t ncol = (int64_t)st.tp * st.bR;
+      T* Z = ar.get_n<T>(ncol * a_out);
+      theta_t(st, EL[c], Q, Z, a_out);
+      const double nrm = host_norm(Z, ncol * a_out);
+      FP_CHECK(nrm > 0, FPEPS_ERR_NUMERIC, "re-canonicalisation: left environment vanished");
+      scale_by_inv<T>(s, Z, ncol * a_out, e->d_scal);
+      EL[c + 1] = env_from_vectors(mem, Z, a_out, st.bR, st.tp, st.nA[2], st.nW[2]);
+      FP_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+
+  // Right-to-left variational fit with controlled bond expansion (Fig. 3-5); pass p of the
+  // row draws its CBE sketch at generator stage 1 + 16 (p - 1).
   double fit(int row, const fpeps_rsvd_params& prm, std::vector<T*>& Nvec, std::vector<int>& abond,
-             std::vector<Env3>& EL, T* Nlast, std::vector<void*>& T_new, std::vector<int>& tb_new, Arena& rowmem) {
+             std::vector<Env3>& EL, T* Nlast, std::vector<void*>& T_new, std::vector<int>& tb_new, Arena& rowmem,
+             int pass) {
     fpeps_env* e = env;
     const int Ly = e->cfg.Ly;
     const int chi = e->cfg.chi;
@@ -1155,7 +1236,7 @@ struct Engine : EngineBase {
         const int k = (int)std::min<int64_t>({(int64_t)ct + prm.oversample, rows_a, cols_a});
         T* omega = ar.get_n<T>(cols_a * k);
         gaussian_sketch<T>(s, omega, cols_a, k, cols_a, nullptr, e->cfg.seed, (uint64_t)e->layer,
-                           (uint64_t)c | (1ull << 16), w3);
+                           (uint64_t)c | ((uint64_t)(1 + 16 * (pass - 1)) << 16), w3);
         const int kmax = k;
         T* tmpA = ar.get_n<T>(std::max<int64_t>(a_eff, na) * kmax);
         T* Xp = ar.get_n<T>(std::max(cols_a, rows_a) * kmax);

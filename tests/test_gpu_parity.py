@@ -69,7 +69,7 @@ TF32X3_OVER_F32 = 12
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 1e-5), ("tf32x3", 1e-5 * TF32X3_OVER_F32)])
-@pytest.mark.parametrize("n_fit", [0, 1])
+@pytest.mark.parametrize("n_fit", [0, 1, 2, 3])
 def test_truncated_4x4_matches_oracle_algorithm(fp, prec, tol, n_fit):
     """Truncated regime (chi=12 < exact bonds): same algorithm, same Omega, both sides.
 
@@ -156,6 +156,33 @@ def test_site_maps_all_ops_against_oracle(fp, prec, tol):
         assert abs(lhs - rhs) <= 10 * tol * (abs(lhs) + np.linalg.norm(y1) * np.linalg.norm(outs[0])), c
         lhs, rhs = ip(z3, outs[2]), ip(env.apply_theta_op(3, c, er, z3, (dD, a)), x2)
         assert abs(lhs - rhs) <= 10 * tol * (abs(lhs) + np.linalg.norm(z3) * np.linalg.norm(outs[2])), c
+    env.close()
+
+
+@pytest.mark.parametrize("n_fit", [2, 3])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("tf32x3", 1e-4)])
+def test_further_fit_passes_match_oracle(fp, n_fit, prec, tol):
+    """n_fit passes of the CBE fit, each after the first starting from the previous one
+    re-canonicalised left to right: kept spectra of every bond after the last pass, the row's
+    log-scale and the boundary shapes against the oracle's absorb_row (truncated regime,
+    D=3, chi=20; the decaying PEPS separates kept from discarded singular values)."""
+    peps = L.decaying_peps(4, 4, 3, 4, seed=7)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=7))
+    T, _ = B.first_row_boundary(peps[0], pepo[0])
+    prm_o = B.RsvdParams(oversample=6, power_iters=2, n_fit=n_fit)
+    res = B.absorb_row(T, peps[1], pepo[1], 20, prm_o, seed=5, layer=1, row=1)
+    env = _env(fp, peps, pepo, D=3, w=4, chi=20, prec=prec, seed=5)
+    fp.fpeps_absorb_row(env.h, 0, 1)
+    fp.fpeps_absorb_row(env.h, 1, 1)
+    st = fp.fpeps_compress_rsvd(env.h, fp.params(6, 2, 0, n_fit, 0))
+    assert abs(st.log_scale - res.log_scale) < tol
+    for c in range(3):
+        sv = np.array(fp.fpeps_bond_spectrum(env.h, 1, c))
+        ref = np.asarray(res.fit_spectra[c])
+        assert sv.shape == ref.shape, c
+        assert np.abs(sv - ref).max() <= tol * ref.max(), c
+    for c in range(4):
+        assert fp.fpeps_boundary_shape(env.h, c) == res.T[c].shape
     env.close()
 
 
