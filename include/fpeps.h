@@ -120,7 +120,8 @@ typedef struct fpeps_env fpeps_env;
  *              compression (zip-up rSVD, CBE rSVD, SVD of the fitted tensor) runs
  *              sector by sector in the charge of the bond it cuts, with one global
  *              truncation; a boundary imported by fpeps_import_boundary carries
- *              no charges (compression then returns FPEPS_ERR_STATE).
+ *              the charges of its checkpoint's charge section (without one,
+ *              compression returns FPEPS_ERR_STATE).
  *   dtype_in   0 = float64, 1 = float32.
  *   cuda_stream   cudaStream_t on which all work is enqueued (NULL = default).
  *   alloc      device allocator or NULL.
@@ -192,7 +193,10 @@ fpeps_status fpeps_expect(fpeps_env* env, const fpeps_rsvd_params* params, doubl
  * paper has no counterpart: this is the library's restart format (the boundary
  * MPS of Sec. II after the rows absorbed so far, with its accumulated scale).
  * Layout: int64 header {magic, Ly, next_row, layer, elem_bytes, bond[Ly+1],
- * phys[Ly]}, double log_scale, then the tensors T_c in compute precision.
+ * phys[Ly]}, double log_scale, then the tensors T_c in compute precision; in
+ * the charge-sector mode (symmetry = 1) a charge section follows: int64 magic
+ * 0x3151425350455046 ("FPEPSBQ1"), then for every bond c = 0..Ly its bond[c]
+ * U(1) x U(1) charge pairs as int32, zero-padded to a multiple of 8 bytes.
  *   host_buf  host memory of *bytes bytes, or NULL: then *bytes receives the
  *             required size and nothing is copied.
  * A staged row that has not been compressed yet is not part of the checkpoint.
@@ -204,8 +208,11 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
 /* Load a boundary (same layout as fpeps_export_boundary, from any source with
  * the right shapes) and make `next_row` the next row to absorb in `layer`. The
  * paper has no counterpart: this restarts a sweep from a stored boundary MPS
- * (Sec. II). Errors: FPEPS_ERR_ARG (bad magic, element size, lattice width, end
- * bonds or byte count; next_row outside 1..Lx-1), FPEPS_ERR_STATE (layer 1 without
+ * (Sec. II). A charge section, if present, gives the bond charges (only an env
+ * with symmetry = 1 accepts one). Errors: FPEPS_ERR_ARG (bad magic, element
+ * size, lattice width, end bonds or byte count; unknown or truncated data after
+ * the tensors; charges for an env without charge sectors; next_row outside
+ * 1..Lx-1), FPEPS_ERR_STATE (layer 1 without
  * an operator PEPO), FPEPS_ERR_OOM, FPEPS_ERR_CUDA. Bundles that do not match the
  * up legs of row `next_row` are reported by the next fpeps_compress_rsvd or
  * closing fpeps_absorb_row (FPEPS_ERR_ARG).

@@ -76,6 +76,7 @@ void prof_end(ProfToken& t, cudaStream_t s) {
 namespace {
 
 const int64_t kMagic = 0x3144425350455046LL;   // "FPEPSBD1"
+const int64_t kQMagic = 0x3151425350455046LL;  // "FPEPSBQ1": optional bond-charge section
 
 template <class F>
 fpeps_status guard(fpeps_env* env, F&& f) {
@@ -403,6 +404,17 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
       n[c] = (size_t)env->tb[c] * env->tphys[c] * env->tb[c + 1];
       total += n[c] * env->elem;
     }
+    // charge-sector mode: the bonds' charge pairs follow the tensors
+    const bool with_q = (int)env->qT.size() == Ly + 1;
+    const size_t tensors_end = total;
+    size_t nq = 0;
+    if (with_q) {
+      for (int c = 0; c <= Ly; ++c) {
+        if ((int64_t)env->qT[c].size() != 2 * (int64_t)env->tb[c]) throw Error{FPEPS_ERR_STATE, "bond charges out of step"};
+        nq += env->qT[c].size();
+      }
+      total += sizeof(int64_t) + ((nq * sizeof(int32_t) + 7) & ~(size_t)7);
+    }
     if (!host_buf) {
       *bytes = total;
       return;
@@ -418,6 +430,15 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
     for (int c = 0; c < Ly; ++c) {
       FP_CUDA(cudaMemcpyAsync(p + off, env->T[c], n[c] * env->elem, cudaMemcpyDeviceToHost, env->stream));
       off += n[c] * env->elem;
+    }
+    if (with_q) {
+      std::memcpy(p + tensors_end, &fpeps::kQMagic, sizeof(int64_t));
+      int32_t* q = (int32_t*)(p + tensors_end + sizeof(int64_t));
+      for (int c = 0; c <= Ly; ++c) {
+        std::memcpy(q, env->qT[c].data(), env->qT[c].size() * sizeof(int32_t));
+        q += env->qT[c].size();
+      }
+      std::memset(q, 0, (char*)(p + total) - (char*)q);
     }
     FP_CUDA(cudaStreamSynchronize(env->stream));
     *bytes = total;
@@ -459,6 +480,30 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
       total += (size_t)tb[c] * ph[c] * tb[c + 1] * env->elem;
     }
     if (bytes < total) throw Error{FPEPS_ERR_ARG, "buffer shorter than its header says"};
+    // optional bond charges after the tensors (charge-sector mode)
+    std::vector<std::vector<int32_t>> qT;
+    if (bytes >= total + sizeof(int64_t)) {
+      size_t nq = 0;
+      for (int c = 0; c <= Ly; ++c) nq += 2 * (size_t)tb[c];
+      std::vector<char> tail(bytes - total);
+      if (on_dev) {
+        FP_CUDA(cudaMemcpyAsync(tail.data(), src + total, tail.size(), cudaMemcpyDeviceToHost, env->stream));
+        FP_CUDA(cudaStreamSynchronize(env->stream));
+      } else {
+        std::memcpy(tail.data(), src + total, tail.size());
+      }
+      int64_t qm = 0;
+      std::memcpy(&qm, tail.data(), sizeof(int64_t));
+      if (qm != fpeps::kQMagic) throw Error{FPEPS_ERR_ARG, "unknown data after the boundary tensors"};
+      if (env->cfg.symmetry != 1) throw Error{FPEPS_ERR_ARG, "bond charges given to an env without charge sectors"};
+      if (tail.size() < sizeof(int64_t) + nq * sizeof(int32_t)) throw Error{FPEPS_ERR_ARG, "bond charges truncated"};
+      const int32_t* q = (const int32_t*)(tail.data() + sizeof(int64_t));
+      qT.assign(Ly + 1, {});
+      for (int c = 0; c <= Ly; ++c) {
+        qT[c].assign(q, q + 2 * tb[c]);
+        q += 2 * tb[c];
+      }
+    }
     for (void* q : env->T) env->al.put(q);
     env->T.assign(Ly, nullptr);
     size_t off = head;
@@ -473,7 +518,7 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
     if (!on_dev) FP_CUDA(cudaStreamSynchronize(env->stream));
     env->tb = tb;
     env->tphys = ph;
-    env->qT.clear();   // a checkpoint carries no charges
+    env->qT = qT;      // empty unless the checkpoint carries bond charges
     env->layer = layer;
     env->next_row = next_row;
     env->state = fpeps::RowState::Ready;

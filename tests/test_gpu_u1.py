@@ -109,3 +109,49 @@ def test_u1_expect_public_api(fp):
     assert sn == sn_o                       # sign and ln|.| of <psi|H|psi>
     assert abs(ln - ln_o) < 1e-9
     assert abs(val - e_o) <= 1e-9 * abs(e_o)
+
+
+def test_u1_checkpoint_carries_bond_charges(fp):
+    """A 4-row lattice in the charge-sector mode: the sweep stopped after row 1, its boundary
+    exported (with the bond charges) and imported into a fresh env, then rows 2 and 3, gives the
+    uninterrupted sweep's value; a dense env refuses the charged checkpoint."""
+    Lx, Ly, D, seed = 4, 4, 2, 5
+    peps, ch = u1.u1_peps(Lx, Ly, D, seed)
+    qpeps = [[u1.peps_leg_charges(ch, Lx, Ly, r, c) for c in range(Ly)] for r in range(Lx)]
+    ham = L.hubbard_hamiltonian(Lx, Ly, seed)
+    W, qW = L.fsm_pepo(ham), u1.hubbard_pepo_charges(ham)
+    prm = fp.params(4, 2, 2, 1, 0)
+
+    def new_env():
+        return fp.Env(peps, W, D=D, p=4, w=6, chi=8, prec="f64", seed=seed, charges=fp.pack_charges(qpeps, qW))
+
+    env = new_env()
+    try:
+        for r in range(Lx):
+            fp.fpeps_absorb_row(env.h, r, 1)
+            if 0 < r < Lx - 1:
+                fp.fpeps_compress_rsvd(env.h, prm)
+            if r == 1:
+                blob = fp.fpeps_export_boundary(env.h)
+        ref = fp.fpeps_sweep_value(env.h)
+    finally:
+        env.close()
+    env = new_env()
+    try:
+        fp.fpeps_import_boundary(env.h, blob, 2, 1)
+        for r in range(2, Lx):
+            fp.fpeps_absorb_row(env.h, r, 1)
+            if r < Lx - 1:
+                fp.fpeps_compress_rsvd(env.h, prm)
+        got = fp.fpeps_sweep_value(env.h)
+    finally:
+        env.close()
+    assert got[0] == ref[0]
+    assert abs(got[1] - ref[1]) < 1e-12
+    dense = fp.Env(peps, W, D=D, p=4, w=6, chi=8, prec="f64", seed=seed)
+    try:
+        with pytest.raises(fp.FpepsError) as ei:
+            fp.fpeps_import_boundary(dense.h, blob, 2, 1)
+        assert ei.value.status == 1   # FPEPS_ERR_ARG
+    finally:
+        dense.close()

@@ -120,3 +120,48 @@ def test_second_pass_uses_its_own_sketch_stage():
     from the first's, and neither collides with the zip-up's (0) or the gauge's (2)."""
     assert [B.fit_stage(p) for p in (1, 2, 3)] == [1, 17, 33]
     assert len({0, 2, B.fit_stage(1), B.fit_stage(2), B.fit_stage(3)}) == 5
+
+
+def _broken_factor_not_carried(T, Arow, Wrow, F):
+    """Planted mistake: each site is split by QR but the factor is dropped instead of carried."""
+    Ly = len(F)
+    EL = np.ones((1, 1, 1))
+    N, ELs = [], [EL]
+    for c in range(Ly - 1):
+        X = F[c]
+        a1, dDn, ac = X.shape
+        Q = B.orth(X.reshape(a1 * dDn, ac))
+        Nc = Q.reshape(a1, dDn, ac)
+        N.append(Nc)
+        el = np.moveaxis(B.theta_t(EL, T[c], Arow[c], Wrow[c], Nc), -1, 0)
+        EL = el / np.linalg.norm(el)
+        ELs.append(EL)
+    N.append(F[Ly - 1] / np.linalg.norm(F[Ly - 1]))
+    return N, ELs
+
+
+def _broken_old_environments(T, Arow, Wrow, F):
+    """Planted mistake: the isometries are re-canonicalised but the environments are built
+    from the fitted (right-canonical) tensors instead of the new left isometries."""
+    N, _ = B.recanonicalize(T, Arow, Wrow, F)
+    EL = np.ones((1, 1, 1))
+    ELs = [EL]
+    for c in range(len(F) - 1):
+        el = np.moveaxis(B.theta_t(EL, T[c], Arow[c], Wrow[c], F[c]), -1, 0)
+        EL = el / np.linalg.norm(el)
+        ELs.append(EL)
+    return N, ELs
+
+
+@pytest.mark.parametrize("broken", [_broken_factor_not_carried, _broken_old_environments])
+def test_planted_recanonicalisation_mistakes_are_caught(broken):
+    """Each planted mistake breaks the state-and-environment pin above on a truncated row."""
+    T, Arow, Wrow = _row_setup(1)
+    prm = B.RsvdParams(oversample=4, power_iters=1)
+    N, ELs, _, _ = B.zipup(T, Arow, Wrow, 8, prm, seed=1, layer=1, row=1)
+    F, _, _ = B.cbe_fit(T, Arow, Wrow, N, ELs, 8, prm, seed=1, layer=1, row=1)
+    N2, ELs2 = broken(T, Arow, Wrow, F)
+    same_state = np.allclose(_mps_vector(N2), _mps_vector(F), atol=1e-10)
+    envs_ok = all(a.shape == b.shape and np.allclose(a, b, atol=1e-10)
+                  for a, b in zip(ELs2, _explicit_envs(T, Arow, Wrow, N2)))
+    assert not (same_state and envs_ok)
