@@ -79,8 +79,11 @@ typedef struct {
   fpeps_precision prec;  /* contraction arithmetic */
   uint64_t seed;         /* key of the Gaussian sketches */
   int32_t symmetry;      /* 0 = dense, 1 = U(1) x U(1) charge sectors */
-  int32_t n_envs;        /* 1 (batched environments: not built) */
+  int32_t n_envs;        /* independent environments in the handle, 1 .. FPEPS_MAX_ENVS
+                            (see fpeps_env_select) */
 } fpeps_config;
+
+#define FPEPS_MAX_ENVS 1024
 
 /* rSVD / CBE settings (Sec. IV). Zero-initialised fields take the defaults in
  * brackets where stated. */
@@ -128,8 +131,8 @@ typedef struct fpeps_env fpeps_env;
  * The inputs are copied (and converted to the compute precision) before the
  * call returns; the caller keeps ownership of its buffers.
  * Errors: FPEPS_ERR_ARG (bad sizes/pointers), FPEPS_ERR_OOM, FPEPS_ERR_CUDA,
- * FPEPS_ERR_UNSUPPORTED (n_envs != 1); FPEPS_ERR_ARG also when symmetry is not 0 or 1 or charges_host
- * does not match it. */
+ * FPEPS_ERR_ARG also when n_envs is outside 1 .. FPEPS_MAX_ENVS, when symmetry is not 0 or 1, or
+ * when charges_host does not match it. */
 fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, const void* pepo_dev,
                               const int32_t* charges_host, int32_t dtype_in, void* cuda_stream,
                               const fpeps_allocator* alloc, fpeps_env** out);
@@ -222,6 +225,17 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
  * copies have executed. */
 fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t bytes, int32_t next_row,
                                    int32_t layer);
+
+/* Select environment e (0 .. n_envs - 1) of the handle: every later call
+ * (absorb, compress, sweep value, contract, expect, checkpoints, spectra, site
+ * maps) acts on it until the next select. The environments of one handle are
+ * independent sweeps over the same lattice (Sec. V computes sixteen such
+ * environments): each has its own boundary, sweep state and value, and its own
+ * Gaussian sketches, since its index enters the generator counter (word 3 =
+ * row | e << 16); they share the lattice, the staged sandwich data, the
+ * engine's scratch and the stream. Environment 0 is selected at creation.
+ * Selecting costs no device work. Errors: FPEPS_ERR_ARG (e out of range). */
+fpeps_status fpeps_env_select(fpeps_env* env, int32_t e);
 
 /* Last error message of the env (never NULL; "" when none). */
 const char* fpeps_last_error(const fpeps_env* env);

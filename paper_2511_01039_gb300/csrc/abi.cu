@@ -234,12 +234,14 @@ fpeps_status fpeps_env_create(const fpeps_config* cfg, const void* peps_dev, con
   if (c.prec < FPEPS_F64 || c.prec > FPEPS_BF16X3) return FPEPS_ERR_ARG;
   if (dtype_in != 0 && dtype_in != 1) return FPEPS_ERR_ARG;
   if (c.Ly > 4096 || c.Lx > 4096 || c.D > 64 || c.p > 64 || c.w > 64) return FPEPS_ERR_ARG;
-  if (c.n_envs != 1) return FPEPS_ERR_UNSUPPORTED;
+  if (c.n_envs < 1 || c.n_envs > FPEPS_MAX_ENVS) return FPEPS_ERR_ARG;
   if (c.symmetry != 0 && c.symmetry != 1) return FPEPS_ERR_ARG;
   if ((c.symmetry == 1) != (charges_host != nullptr)) return FPEPS_ERR_ARG;
   fpeps_env* env = new (std::nothrow) fpeps_env();
   if (!env) return FPEPS_ERR_OOM;
   env->cfg = c;
+  env->slots.resize((size_t)c.n_envs);
+  env->cur = 0;
   env->elem = c.prec == FPEPS_F64 ? 8 : 4;
   env->stream = (cudaStream_t)cuda_stream;
   env->al.stream = env->stream;
@@ -528,6 +530,45 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
 
 const char* fpeps_last_error(const fpeps_env* env) { return env ? env->err.c_str() : "env is NULL"; }
 
+fpeps_status fpeps_env_select(fpeps_env* env, int32_t e) {
+  return fpeps::guard(env, [&] {
+    fpeps::check_env(env);
+    if (e < 0 || e >= (int32_t)env->slots.size()) throw Error{FPEPS_ERR_ARG, "environment index out of range"};
+    if (e == env->cur) return;
+    // park the selected environment's state, bring in environment e's
+    fpeps_env::Slot& out = env->slots[env->cur];
+    out.T.swap(env->T);
+    out.tb.swap(env->tb);
+    out.tphys.swap(env->tphys);
+    out.qT.swap(env->qT);
+    out.log_scale = env->log_scale;
+    out.next_row = env->next_row;
+    out.layer = env->layer;
+    out.state = env->state;
+    out.staged_row = env->staged_row;
+    out.have_value = env->have_value;
+    out.value_log = env->value_log;
+    out.value_sign = env->value_sign;
+    std::swap(out.spectra, env->spectra);
+    fpeps_env::Slot& in = env->slots[e];
+    env->T.swap(in.T);
+    env->tb.swap(in.tb);
+    env->tphys.swap(in.tphys);
+    env->qT.swap(in.qT);
+    env->log_scale = in.log_scale;
+    env->next_row = in.next_row;
+    env->layer = in.layer;
+    env->state = in.state;
+    env->staged_row = in.staged_row;
+    env->have_value = in.have_value;
+    env->value_log = in.value_log;
+    env->value_sign = in.value_sign;
+    std::swap(env->spectra, in.spectra);
+    in = fpeps_env::Slot{};
+    env->cur = e;
+  });
+}
+
 void fpeps_env_destroy(fpeps_env* env) {
   if (!env) return;
   try {
@@ -537,6 +578,9 @@ void fpeps_env_destroy(fpeps_env* env) {
       for (auto& sd : env->sand[layer])
         for (void* b : sd.bufs) env->al.put(b);
     for (void* p : env->T) env->al.put(p);
+    for (size_t i = 0; i < env->slots.size(); ++i)
+      if ((int)i != env->cur)
+        for (void* p : env->slots[i].T) env->al.put(p);
     env->al.put(env->peps);
     env->al.put(env->pepo[0]);
     env->al.put(env->pepo[1]);

@@ -841,7 +841,7 @@ struct Engine : EngineBase {
     std::vector<T*> ELvec(Ly, nullptr);
     EL[0] = unit_env(rowmem);
     double log_s = 0.0;
-    const uint64_t w3 = (uint64_t)row;
+    const uint64_t w3 = (uint64_t)row | ((uint64_t)env->cur << 16);   // row | environment << 16
 
     // ---------------- zip-up, left to right
     for (int c = 0; c < Ly - 1; ++c) {
@@ -1192,7 +1192,7 @@ struct Engine : EngineBase {
     const int Ly = e->cfg.Ly;
     const int chi = e->cfg.chi;
     const int chi_t = prm.chi_tilde > 0 ? prm.chi_tilde : (chi + 9) / 10;
-    const uint64_t w3 = (uint64_t)row;
+    const uint64_t w3 = (uint64_t)row | ((uint64_t)env->cur << 16);   // row | environment << 16
     // centre M [a_prev][Dn][a_c] as vectors (a_prev of them)
     Arena mmem = arena();
     int a_prev = abond[Ly - 1];
@@ -1432,7 +1432,7 @@ struct Engine : EngineBase {
     const int Ly = e->cfg.Ly;
     const int chi = e->cfg.chi;
     const int chi_t = prm.chi_tilde > 0 ? prm.chi_tilde : (chi + 9) / 10;
-    const uint64_t w3 = (uint64_t)row;
+    const uint64_t w3 = (uint64_t)row | ((uint64_t)env->cur << 16);   // row | environment << 16
     Arena mmem = arena();
     int a_prev = abond[Ly - 1];
     int a_c = 1;

@@ -67,6 +67,28 @@ struct fpeps_env {
   int value_sign = 0;
 
   fpeps::Spectrum spectra;
+
+  // n_envs > 1: independent environments over the same lattice. Each keeps its own
+  // boundary, sweep state, value and spectra (the fields above, for the selected one;
+  // the others parked here) and its own sketch streams (its index enters the generator
+  // counter); the lattice, the staged sandwich data, the engine's scratch and the
+  // stream are shared.
+  struct Slot {
+    std::vector<void*> T;
+    std::vector<int> tb, tphys;
+    std::vector<std::vector<int32_t>> qT;
+    double log_scale = 0.0;
+    int next_row = 0, layer = 0;
+    fpeps::RowState state = fpeps::RowState::Ready;
+    int staged_row = -1;
+    bool have_value = false;
+    double value_log = 0.0;
+    int value_sign = 0;
+    fpeps::Spectrum spectra;
+  };
+  std::vector<Slot> slots;   // n_envs entries; slots[cur] is stale while cur is selected
+  int cur = 0;
+
   fpeps::EngineBase* engine = nullptr;
   int* d_info = nullptr;    // device status words
   int* h_info = nullptr;    // pinned host mirror

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fpeps_export_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "fpeps_import_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32, C.c_int32]),
     "fpeps_last_error": (C.c_char_p, [C.c_void_p]),
+    "fpeps_env_select": (C.c_int, [C.c_void_p, C.c_int32]),
     "fpeps_env_destroy": (None, [C.c_void_p]),
     "fpeps_boundary_shape": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32)]),
@@ -195,6 +196,10 @@ def fpeps_import_boundary(env, blob: bytes, next_row: int, layer: int):
     _check(env, lib().fpeps_import_boundary(env, buf, len(blob), next_row, layer))
 
 
+def fpeps_env_select(env, e: int):
+    _check(env, lib().fpeps_env_select(env, e))
+
+
 def fpeps_last_error(env) -> str:
     return lib().fpeps_last_error(env).decode()
 
@@ -312,7 +317,7 @@ class Env:
     """
 
     def __init__(self, peps, pepo, *, D, p, w, chi, prec="f64", seed=0, stream=None, use_torch_allocator=True,
-                 charges=None):
+                 charges=None, n_envs=1):
         import numpy as np
         import torch
         self.torch = torch
@@ -324,7 +329,8 @@ class Env:
         wk = None
         if pepo is not None:
             wk = torch.cat([torch.as_tensor(np.asarray(t), dtype=dt).reshape(-1) for row in pepo for t in row]).to(self.dev)
-        self.cfg = fpeps_config(Lx, Ly, D, p, w, chi, PRECISIONS[prec], seed, 1 if charges is not None else 0, 1)
+        self.cfg = fpeps_config(Lx, Ly, D, p, w, chi, PRECISIONS[prec], seed, 1 if charges is not None else 0,
+                                n_envs)
         self.elem = 8 if prec == "f64" else 4
         self.alloc = TorchAllocator(self.dev) if use_torch_allocator else None
         torch.cuda.synchronize(self.dev)
@@ -341,6 +347,10 @@ class Env:
             self.close()
         except Exception:
             pass
+
+    def select(self, e):
+        """Make environment e of the handle the one later calls act on."""
+        fpeps_env_select(self.h, e)
 
     def norm(self, params):
         return fpeps_contract_norm(self.h, params)

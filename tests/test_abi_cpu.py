@@ -57,13 +57,15 @@ def test_create_rejects_bad_arguments_without_gpu(built):
     cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 2, 1)       # unknown symmetry
     st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
     assert st == 1
-    cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 0, 2)       # batched environments not built
-    st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
-    assert st == 7
+    for n_envs in (0, -1, 1025):                                  # environments: 1 .. FPEPS_MAX_ENVS
+        cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 0, 0, 0, n_envs)
+        st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
+        assert st == 1 and not out.value
     cfg = fpeps.fpeps_config(3, 3, 2, 4, 1, 8, 9, 0, 0, 1)       # bad precision enum
     st = fpeps.lib().fpeps_env_create(ctypes.byref(cfg), 1, None, None, 0, None, None, ctypes.byref(out))
     assert st == 1
     assert fpeps.lib().fpeps_absorb_row(None, 0, 0) == 1
+    assert fpeps.lib().fpeps_env_select(None, 0) == 1
     assert fpeps.lib().fpeps_last_error(None) == b"env is NULL"
     fpeps.lib().fpeps_env_destroy(None)
 

@@ -186,6 +186,40 @@ def test_further_fit_passes_match_oracle(fp, n_fit, prec, tol):
     env.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("tf32x3", 1e-3)])
+def test_independent_environments_of_one_handle(fp, prec, tol):
+    """n_envs = 3 over one lattice, swept row by row in interleaved order (select 0, 1, 2 for
+    every row): environment e gives the oracle's sweep with environment index e in its sketch
+    counters, and the three values differ (independent sketches at a truncation that the
+    sketch decides: oversampling 2, no power iteration; the oracle's three values lie 2.5e-3 and
+    3.8e-3 apart in ln|value|)."""
+    peps = L.decaying_peps(4, 4, 2, 4, seed=3)
+    pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=3))
+    prm_o = B.RsvdParams(oversample=2, power_iters=0, n_fit=1)
+    env = fp.Env(peps, pepo, D=2, p=4, w=4, chi=10, prec=prec, seed=5, n_envs=3)
+    try:
+        for r in range(4):
+            for e in range(3):
+                env.select(e)
+                fp.fpeps_absorb_row(env.h, r, 1)
+                if 0 < r < 3:
+                    fp.fpeps_compress_rsvd(env.h, fp.params(2, 0, 0, 1, 0))
+        got = []
+        for e in (2, 0, 1):
+            env.select(e)
+            got.append((e, fp.fpeps_sweep_value(env.h)))
+        with pytest.raises(fp.FpepsError):
+            env.select(3)
+    finally:
+        env.close()
+    for e, (sg, lg) in got:
+        so, lo = B.contract(peps, pepo, 10, prm_o, seed=5, layer=1, env=e)
+        assert sg == so, e
+        assert abs(lg - lo) < tol, e
+    logs = sorted(v[1] for _, v in got)
+    assert logs[1] - logs[0] > 1e-3 and logs[2] - logs[1] > 1e-3
+
+
 def test_zip_spectrum_and_apply_theta_match_oracle(fp):
     peps = L.random_peps(4, 4, 2, 4, seed=4)
     pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=4))
