@@ -13,7 +13,8 @@ It restates, slowly and in double precision, what the GPU path computes:
                  column-wise contraction.
 * ``boundary`` - the boundary-MPS environment approximation (Sec. II) with
                  rSVD compression (Sec. IV, Halko et al. Example 1.6) and the
-                 CBE variational fit whose A*Omega follows Fig. 5.
+                 CBE variational fit whose A*Omega follows Fig. 5 (n_fit passes,
+                 re-canonicalised left to right between them).
 * ``symmetric`` - the U(1) x U(1) block-sparse mode (Sec. III quantum-number
                  slicing, Sec. V symmetric Hubbard runs): the zip-up with a
                  sector-wise rSVD and one global truncation, and the CBE fit

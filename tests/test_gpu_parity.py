@@ -220,6 +220,27 @@ def test_independent_environments_of_one_handle(fp, prec, tol):
     assert logs[1] - logs[0] > 1e-3 and logs[2] - logs[1] > 1e-3
 
 
+@pytest.mark.parametrize("Lx,Ly,prec,tol", [(1, 1, "f64", 1e-10), (1, 2, "f64", 1e-10), (1, 3, "f64", 1e-10),
+                                            (2, 1, "f64", 1e-10), (2, 3, "f64", 1e-10), (3, 1, "f64", 1e-10),
+                                            (3, 2, "f64", 1e-10), (2, 3, "tf32x3", 1e-5), (3, 2, "tf32x3", 1e-5)])
+def test_degenerate_lattice_shapes_against_brute_force(fp, Lx, Ly, prec, tol):
+    """The method's degenerate cases through the public fpeps_expect: one row (closed at once
+    against the trivial boundary), two rows (row 0 exact, then closed: no compression), one
+    column (every Theta_c has a single column), two columns (zip-up of one site plus the last
+    site); D=2, FSM PEPO with two hopping channels, chi above every bond. The split-precision
+    mode runs the shapes whose sites the 3x3 tests already send to the tensor-core sandwich."""
+    peps = L.random_peps(Lx, Ly, 2, 4, seed=4)
+    pepo = L.fsm_pepo(L.random_hamiltonian(Lx, Ly, 4, 2, seed=4))
+    num, den = N.brute_force_expectation(peps, pepo)
+    env = _env(fp, peps, pepo, D=2, w=4, chi=16, prec=prec, seed=2)
+    try:
+        val, sn, ln = env.expect(fp.params(10, 0, 0, 1, 1))
+    finally:
+        env.close()
+    assert abs(val / (num / den) - 1) < tol
+    assert sn == (1 if num >= 0 else -1)
+
+
 def test_zip_spectrum_and_apply_theta_match_oracle(fp):
     peps = L.random_peps(4, 4, 2, 4, seed=4)
     pepo = L.fsm_pepo(L.random_hamiltonian(4, 4, 4, 2, seed=4))
