@@ -191,7 +191,9 @@ def roofline_of(kind: str, d: dict, prec: str, peaks: dict) -> dict:
     tflops = d["flops"] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
     gbs = d["bytes"] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
     traffic = None
-    if kind in DRAM_PER_ALG_BYTE and d["launches"]:
+    # the ratios come from captures of the 3xTF32 kernels; the 3xBF16 GEMM is another kernel
+    captured = not (prec == "bf16x3" and kind == "gemm_tc_tf32x3")
+    if kind in DRAM_PER_ALG_BYTE and d["launches"] and captured:
         traffic = DRAM_PER_ALG_BYTE[kind] * d["bytes"] / d["launches"]
     intensity = d["flops"] / d["bytes"] if d["bytes"] > 0 else float("inf")   # flop per byte
     tensor_kinds = ("gemm_tc_tf32x3", "sandwich") if prec in ("tf32x3", "bf16x3") else ("gemm_tc_tf32x3",)
