@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
             bf16_split(__uint_as_float(v.y), h[1], l[1]);
             bf16_split(__uint_as_float(v.z), h[2], l[2]);
             bf16_split(__uint_as_float(v.w), h[3], l[3]);
-            h2[2 * c] = h[0] | (h[1] << 16);
-            h2[2 * c + 1] = h[2] | (h[3] << 16);
-            l2[2 * c] = l[0] | (l[1] << 16);
-            l2[2 * c + 1] = l[2] | (l[3] << 16);
+            h2[2 * c] = bf16_pack(h[0], h[1]);
+            h2[2 * c + 1] = bf16_pack(h[2], h[3]);
+            l2[2 * c] = bf16_pack(l[0], l[1]);
+            l2[2 * c + 1] = bf16_pack(l[2], l[3]);
           }
           const uint32_t ta = tmem + lane_base + abase + (uint32_t)(as * AW);
           tmem_st16(ta, h2);
@@ -442,10 +442,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_tf32x3_t(const __grid_con
 #pragma unroll
             for (int q = 0; q < 8; ++q) bf16_split(f[q], h[q], l[q]);
             const uint32_t off = (uint32_t)j * LB + (uint32_t)(n / 8) * 128 + (uint32_t)(n % 8) * 16;
-            *(uint4*)(h16 + off) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16),
-                                              h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-            *(uint4*)(l16 + off) = make_uint4(l[0] | (l[1] << 16), l[2] | (l[3] << 16),
-                                              l[4] | (l[5] << 16), l[6] | (l[7] << 16));
+            *(uint4*)(h16 + off) = make_uint4(bf16_pack(h[0], h[1]), bf16_pack(h[2], h[3]),
+                                              bf16_pack(h[4], h[5]), bf16_pack(h[6], h[7]));
+            *(uint4*)(l16 + off) = make_uint4(bf16_pack(l[0], l[1]), bf16_pack(l[2], l[3]),
+                                              bf16_pack(l[4], l[5]), bf16_pack(l[6], l[7]));
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();

@@ -231,16 +231,17 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
       : "memory");
 }
 
-// x = hi + lo + O(2^-17 |x|) with hi, lo BF16 (8 significant bits), as bit patterns in the low
-// 16 bits: hi is x rounded on its FP32 bit pattern (add half a BF16 unit, drop the low 16 bits:
-// ties away from zero, like tf32_round), lo the remainder x - hi, exact in FP32, rounded the same
-// way. Two integer instructions per rounding instead of a conversion instruction each.
+// x = hi + lo + O(2^-17 |x|) with hi, lo BF16 (8 significant bits), as FP32 bit patterns whose
+// low 16 bits are zero (the BF16 pattern is the high half): hi is x rounded on its FP32 bit
+// pattern (add half a BF16 unit, drop the low 16 bits: ties away from zero, like tf32_round), lo
+// the remainder x - hi, exact in FP32, rounded the same way. Two integer instructions per
+// rounding instead of a conversion instruction each.
 __device__ __forceinline__ void bf16_split(float x, uint32_t& hi, uint32_t& lo) {
-  const uint32_t hb = (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u;
-  const uint32_t lb = (__float_as_uint(x - __uint_as_float(hb)) + 0x8000u) & 0xFFFF0000u;
-  hi = hb >> 16;
-  lo = lb >> 16;
+  hi = (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u;
+  lo = (__float_as_uint(x - __uint_as_float(hi)) + 0x8000u) & 0xFFFF0000u;
 }
+// two BF16 values of bf16_split into one 32-bit word, a in the low half (one byte permute)
+__device__ __forceinline__ uint32_t bf16_pack(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
 
 // ---------------------------------------------------------------- additions for the sandwich
 // 1-D bulk copy global -> shared (TMA engine), completion signalled on `bar` as tx bytes;
