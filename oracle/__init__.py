@@ -20,6 +20,9 @@ It restates, slowly and in double precision, what the GPU path computes:
                  sector-wise rSVD and one global truncation, and the CBE fit
                  with a sector-wise CBE rSVD and a sector-wise SVD of the
                  fitted tensor, on the dense applications of ``boundary``.
+* ``blocksparse`` - the site application Theta_c X by charge blocks (Sec. III
+                 quantum-number slices): one task per output block of each
+                 of its three contractions, with the task list.
 
 It shares no code with the CUDA path; the only common module is the seeded
 input generator ``synth`` (data, no method arithmetic).

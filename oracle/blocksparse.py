@@ -1,0 +1,143 @@
+"""Block-sparse application of the site matrix Theta_c (oracle; test infrastructure).
+
+The paper cuts its contractions into quantum-number slices (Sec. III): with
+charge-conserving tensors every contraction splits into independent products of
+charge blocks, and each output block is computed by one task that sums the
+block products feeding it, so no two tasks write the same output. This module
+restates the application Y = Theta_c X of the zip-up (Sec. IV, contraction
+pattern 2(a): boundary x vectors, the site sandwich, environment x vectors)
+for the vectors of one sector in that form, with the dense FP64 sandwich
+C[L, U, R, Dn] of ``oracle.network`` as the site tensor, and returns the task
+list with it, so that a block-sparse GPU path can be checked task by task.
+
+Charges are pairs (N_up, N_dn), with the rules of ``oracle.symmetric``:
+  boundary tensor T[t, U, t']:   q_t = Q_U + q_t'
+  sandwich C[L, U, R, Dn]:       Q_L + Q_U = Q_R + Q_Dn
+  left environment EL[a, t, L]:  q_a = q_t + Q_L
+  vectors of sector q:           X[t', R, k] nonzero only where q_t' + Q_R = q,
+                                 Y[a, Dn, k] nonzero only where q_a - Q_Dn = q.
+The three steps and their tasks (one per output block, keyed by its charges):
+  1. G1[t, U, R] = sum_t' T[t, U, t'] X[t', R]: block (q_t, Q_U, Q_R) from the
+     single t' block q_t' = q_t - Q_U (then Q_R = q - q_t');
+  2. G2[t, L, Dn] = sum_{U, R} C[L, U, R, Dn] G1[t, U, R]: block (q_t, Q_L, Q_Dn),
+     q_t + Q_L - Q_Dn = q, summed over the U blocks with R = Q_U + Q_L - Q_Dn;
+  3. Y[a, Dn] = sum_{t, L} EL[a, t, L] G2[t, L, Dn]: block (q_a, Q_Dn),
+     q_a - Q_Dn = q, summed over the (q_t, Q_L) blocks with q_t + Q_L = q_a.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from .network import sandwich_full
+
+
+def charge_groups(q: np.ndarray) -> dict:
+    """Index lists of every charge on a leg: {(N_up, N_dn): ascending indices}."""
+    out: dict = {}
+    for i, x in enumerate(np.asarray(q).reshape(-1, 2).tolist()):
+        out.setdefault(tuple(x), []).append(i)
+    return {k: np.array(v) for k, v in out.items()}
+
+
+def _add(a, b):
+    return (a[0] + b[0], a[1] + b[1])
+
+
+def _sub(a, b):
+    return (a[0] - b[0], a[1] - b[1])
+
+
+def _accumulate(acc, p):
+    """Sum of the block products of one task."""
+    return p if acc is None else acc + p
+
+
+@dataclasses.dataclass
+class Task:
+    step: int          # 1: boundary x vectors, 2: sandwich, 3: environment x vectors
+    out: tuple         # charges of the output block
+    terms: int         # block products summed into it
+    flops: float       # 2 x multiply-adds of those products
+
+
+def theta_blocks(EL, qa, T, qt, qU, qtp, A, W, qsite, X, q):
+    """Y = Theta_c X by charge blocks for the vectors X[t', R, k] of sector q.
+
+    EL[a, t, L] with bond charges qa (a) and qt (t); T[t, U, t'] with qt, qU, qtp;
+    qsite = (Q_L, Q_U, Q_R, Q_Dn) of the site's bundles (Q_U must equal qU).
+    Returns (Y [a, Dn, k], tasks)."""
+    q = tuple(q)
+    C = sandwich_full(A, W)
+    QL, QU, QR, QD = qsite
+    gA, gT, gTp = charge_groups(qa), charge_groups(qt), charge_groups(qtp)
+    gL, gU, gR, gD = charge_groups(QL), charge_groups(QU), charge_groups(QR), charge_groups(QD)
+    k = X.shape[2]
+    tasks = []
+    # 1. boundary x vectors
+    G1 = np.zeros((T.shape[0], T.shape[1], X.shape[1], k))
+    for ctp, itp in gTp.items():
+        cr = _sub(q, ctp)
+        if cr not in gR:
+            continue
+        ir = gR[cr]
+        for cu, iu in gU.items():
+            ct = _add(cu, ctp)
+            if ct not in gT:
+                continue
+            it = gT[ct]
+            blk = np.einsum("tUs,sRk->tURk", T[np.ix_(it, iu, itp)], X[np.ix_(itp, ir)], optimize=True)
+            G1[np.ix_(it, iu, ir)] = blk
+            tasks.append(Task(1, (ct, cu, cr), 1, 2.0 * len(it) * len(iu) * len(itp) * len(ir) * k))
+    # 2. the site sandwich
+    G2 = np.zeros((T.shape[0], C.shape[0], C.shape[3], k))
+    for ct, it in gT.items():
+        for cl, il in gL.items():
+            cd = _sub(_add(ct, cl), q)
+            if cd not in gD:
+                continue
+            idd = gD[cd]
+            acc, terms, fl = None, 0, 0.0
+            for cu, iu in gU.items():
+                cr = _sub(_add(cu, cl), cd)
+                if cr not in gR:
+                    continue
+                ir = gR[cr]
+                p = np.einsum("LURD,tURk->tLDk", C[np.ix_(il, iu, ir, idd)], G1[np.ix_(it, iu, ir)], optimize=True)
+                acc = _accumulate(acc, p)
+                terms += 1
+                fl += 2.0 * len(it) * len(il) * len(iu) * len(ir) * len(idd) * k
+            if acc is not None:
+                G2[np.ix_(it, il, idd)] = acc
+                tasks.append(Task(2, (ct, cl, cd), terms, fl))
+    # 3. environment x vectors
+    Y = np.zeros((EL.shape[0], C.shape[3], k))
+    for ca, ia in gA.items():
+        cd = _sub(ca, q)
+        if cd not in gD:
+            continue
+        idd = gD[cd]
+        acc, terms, fl = None, 0, 0.0
+        for ct, it in gT.items():
+            cl = _sub(ca, ct)
+            if cl not in gL:
+                continue
+            il = gL[cl]
+            p = np.einsum("atL,tLDk->aDk", EL[np.ix_(ia, it, il)], G2[np.ix_(it, il, idd)], optimize=True)
+            acc = _accumulate(acc, p)
+            terms += 1
+            fl += 2.0 * len(ia) * len(it) * len(il) * len(idd) * k
+        if acc is not None:
+            Y[np.ix_(ia, idd)] = acc
+            tasks.append(Task(3, (ca, cd), terms, fl))
+    return Y, tasks
+
+
+def dense_flops(EL, T, A, W, X) -> float:
+    """Multiply-add count x 2 of the same three steps with dense tensors (no blocks)."""
+    C = sandwich_full(A, W)
+    t, u, tp = T.shape
+    r, k = X.shape[1], X.shape[2]
+    a, l, d = EL.shape[0], C.shape[0], C.shape[3]
+    return 2.0 * k * (t * u * tp * r + t * l * u * r * d + a * t * l * d)
