@@ -57,8 +57,10 @@ typedef enum {
  * products. TF32X3 / BF16X3: split-precision products on the tensor cores,
  * a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with FP32 accumulation, the operands split
  * into TF32 (3 x 2^-22 relative error per product) or BF16 (3 x 2^-16) halves.
- * In BF16X3 the boundary and environment GEMMs take the BF16 split; the site
- * sandwich and the tall products of the QR stay 3xTF32 / FP32. */
+ * In BF16X3 every tensor-core GEMM (boundary and environment products, the
+ * QR's tall products, the CBE projectors) takes the BF16 split; the site
+ * sandwich stays 3xTF32, and the calibration columns and unbiased products
+ * run on the FP32 CUDA cores as in TF32X3. */
 typedef enum { FPEPS_F64 = 0, FPEPS_F32 = 1, FPEPS_TF32X3 = 2, FPEPS_BF16X3 = 3 } fpeps_precision;
 
 /* Device-memory provider. alloc(ctx, bytes, stream) returns device memory usable
@@ -84,10 +86,10 @@ typedef struct {
 } fpeps_config;
 
 #define FPEPS_MAX_ENVS 1024
+#define FPEPS_MAX_FIT_PASSES 8
 
 /* rSVD / CBE settings (Sec. IV). Zero-initialised fields take the defaults in
  * brackets where stated. */
-#define FPEPS_MAX_FIT_PASSES 8
 typedef struct {
   int32_t oversample;   /* sketch width = kept bond + oversample            */
   int32_t power_iters;  /* q: applications of A^T A after the first A       */
