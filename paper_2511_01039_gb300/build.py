@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["abi.cu", "engine.cu", "gemm_simt.cu", "gemm_tc.cu", "sandwich.cu", "sandwich_tc.cu", "linalg.cu",
-           "svd_noalloc.cu"]
+           "svd_noalloc.cu", "blocks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
