@@ -228,8 +228,9 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
 fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t bytes, int32_t next_row,
                                    int32_t layer);
 
-/* Task table of the block-sparse application Y = Theta_c X to the vectors of
- * one charge sector q (Sec. III: contractions cut into quantum-number slices
+/* Task table of the block-sparse application Y = Theta_c X (op 0) or
+ * Z = Theta_c^T Y (op 1, the rSVD's transpose) to the vectors of one charge
+ * sector q (Sec. III: contractions cut into quantum-number slices
  * whose outputs do not overlap; Sec. IV: the application of the zip-up, pattern
  * 2(a)). Host code, no device work. With charge-conserving tensors each of the
  * three contractions (1: boundary x vectors, 2: the site sandwich, 3:
@@ -237,18 +238,23 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
  * block, summing the block products that feed it. Charge rules, pairs
  * (N_up, N_dn): T[t, U, t'] q_t = Q_U + q_t'; sandwich Q_L + Q_U = Q_R + Q_Dn;
  * left environment EL[a, t, L] q_a = q_t + Q_L; X[t', R] in sector q where
- * q_t' + Q_R = q.
+ * q_t' + Q_R = q, Y[a, Dn] where q_a - Q_Dn = q. Op 1 runs the mirror steps
+ * (1: environment^T x vectors, 2: the sandwich transposed, 3: boundary^T x
+ * vectors).
  *   qa, qt, qu, qtp, ql, qr, qd  host int32 charge pairs of the legs a, t, U,
  *              t', L, R, Dn (n entries each, pairs interleaved); q the sector.
  *   tasks      host int32 [cap][8]: step (1..3), number of block products,
- *              then the output block's charges: step 1 (t, U, R), step 2
- *              (t, L, Dn), step 3 (a, Dn) and one zero pair; steps in order,
- *              within a step the legs' charges in order of first appearance.
+ *              then the output block's charges: op 0 step 1 (t, U, R), step 2
+ *              (t, L, Dn), step 3 (a, Dn) and one zero pair; op 1 step 1
+ *              (t, L, Dn), step 2 (t, U, R), step 3 (t', R) and one zero pair;
+ *              steps in order, within a step the legs' charges in order of
+ *              first appearance.
  *   flops      host double [cap]: 2 x multiply-adds of the task per vector.
  *   n_inout    in: cap; out: number of tasks. With cap 0 (tasks, flops may be
  *              NULL) only the count is returned.
- * Errors: FPEPS_ERR_ARG (NULL pointer, empty leg, cap too small). */
-fpeps_status fpeps_theta_block_tasks(const int32_t* qa, int32_t na, const int32_t* qt, int32_t nt,
+ * Errors: FPEPS_ERR_ARG (op not 0 or 1, NULL pointer, empty leg, cap too
+ * small). */
+fpeps_status fpeps_theta_block_tasks(int32_t op, const int32_t* qa, int32_t na, const int32_t* qt, int32_t nt,
                                      const int32_t* qu, int32_t nu, const int32_t* qtp, int32_t ntp,
                                      const int32_t* ql, int32_t nl, const int32_t* qr, int32_t nr,
                                      const int32_t* qd, int32_t nd, const int32_t* q, int32_t* tasks,

@@ -8,7 +8,8 @@ restates the application Y = Theta_c X of the zip-up (Sec. IV, contraction
 pattern 2(a): boundary x vectors, the site sandwich, environment x vectors)
 for the vectors of one sector in that form, with the dense FP64 sandwich
 C[L, U, R, Dn] of ``oracle.network`` as the site tensor, and returns the task
-list with it, so that a block-sparse GPU path can be checked task by task.
+list with it, so that a block-sparse GPU path can be checked task by task;
+``theta_t_blocks`` does the same for the transpose application Theta_c^T.
 
 Charges are pairs (N_up, N_dn), with the rules of ``oracle.symmetric``:
   boundary tensor T[t, U, t']:   q_t = Q_U + q_t'
@@ -132,6 +133,79 @@ def theta_blocks(EL, qa, T, qt, qU, qtp, A, W, qsite, X, q):
             Y[np.ix_(ia, idd)] = acc
             tasks.append(Task(3, (ca, cd), terms, fl))
     return Y, tasks
+
+
+def theta_t_blocks(EL, qa, T, qt, qU, qtp, A, W, qsite, Y, q):
+    """Z = Theta_c^T Y by charge blocks for the vectors Y[a, Dn, k] of sector q (q_a - Q_Dn = q).
+    The mirror of theta_blocks (the transpose application of the rSVD, Sec. IV):
+      1. H1[t, L, Dn] = sum_a EL[a, t, L] Y[a, Dn]: block (q_t, Q_L, Q_Dn), q_t + Q_L - Q_Dn = q,
+         from the single a block q_a = q_t + Q_L;
+      2. H2[t, U, R] = sum_{L, Dn} C[L, U, R, Dn] H1[t, L, Dn]: block (q_t, Q_U, Q_R),
+         q_t - Q_U + Q_R = q, summed over the L blocks with Dn = L + U - R;
+      3. Z[t', R] = sum_{t, U} T[t, U, t'] H2[t, U, R]: block (q_t', Q_R), q_t' + Q_R = q,
+         summed over the U blocks with t = U + t'.
+    Returns (Z [t', R, k], tasks)."""
+    q = tuple(q)
+    C = sandwich_full(A, W)
+    QL, QU, QR, QD = qsite
+    gA, gT, gTp = charge_groups(qa), charge_groups(qt), charge_groups(qtp)
+    gL, gU, gR, gD = charge_groups(QL), charge_groups(QU), charge_groups(QR), charge_groups(QD)
+    k = Y.shape[2]
+    tasks = []
+    # 1. environment^T x vectors
+    H1 = np.zeros((T.shape[0], C.shape[0], C.shape[3], k))
+    for ct, it in gT.items():
+        for cl, il in gL.items():
+            ca = _add(ct, cl)
+            cd = _sub(ca, q)
+            if ca not in gA or cd not in gD:
+                continue
+            ia, idd = gA[ca], gD[cd]
+            H1[np.ix_(it, il, idd)] = np.einsum("atL,aDk->tLDk", EL[np.ix_(ia, it, il)], Y[np.ix_(ia, idd)],
+                                                optimize=True)
+            tasks.append(Task(1, (ct, cl, cd), 1, 2.0 * len(ia) * len(it) * len(il) * len(idd) * k))
+    # 2. the site sandwich, transposed
+    H2 = np.zeros((T.shape[0], C.shape[1], C.shape[2], k))
+    for ct, it in gT.items():
+        for cu, iu in gU.items():
+            cr = _add(_sub(q, ct), cu)
+            if cr not in gR:
+                continue
+            ir = gR[cr]
+            acc, terms, fl = None, 0, 0.0
+            for cl, il in gL.items():
+                cd = _sub(_add(cl, cu), cr)
+                if cd not in gD:
+                    continue
+                idd = gD[cd]
+                p = np.einsum("LURD,tLDk->tURk", C[np.ix_(il, iu, ir, idd)], H1[np.ix_(it, il, idd)], optimize=True)
+                acc = _accumulate(acc, p)
+                terms += 1
+                fl += 2.0 * len(it) * len(il) * len(iu) * len(ir) * len(idd) * k
+            if acc is not None:
+                H2[np.ix_(it, iu, ir)] = acc
+                tasks.append(Task(2, (ct, cu, cr), terms, fl))
+    # 3. boundary^T x vectors
+    Z = np.zeros((T.shape[2], C.shape[2], k))
+    for ctp, itp in gTp.items():
+        cr = _sub(q, ctp)
+        if cr not in gR:
+            continue
+        ir = gR[cr]
+        acc, terms, fl = None, 0, 0.0
+        for cu, iu in gU.items():
+            ct = _add(cu, ctp)
+            if ct not in gT:
+                continue
+            it = gT[ct]
+            p = np.einsum("tUs,tURk->sRk", T[np.ix_(it, iu, itp)], H2[np.ix_(it, iu, ir)], optimize=True)
+            acc = _accumulate(acc, p)
+            terms += 1
+            fl += 2.0 * len(it) * len(iu) * len(itp) * len(ir) * k
+        if acc is not None:
+            Z[np.ix_(itp, ir)] = acc
+            tasks.append(Task(3, (ctp, cr), terms, fl))
+    return Z, tasks
 
 
 def dense_flops(EL, T, A, W, X) -> float:

@@ -1,4 +1,4 @@
-// Task tables of the block-sparse site application Y = Theta_c X (host code).
+// Task tables of the block-sparse site applications Y = Theta_c X and Z = Theta_c^T Y (host code).
 //
 // With charge-conserving tensors every contraction of the application (Sec. IV,
 // pattern 2(a) of Sec. III: boundary x vectors, the site sandwich, environment x
@@ -100,20 +100,65 @@ std::vector<BlockTask> theta_tasks(const Groups& gA, const Groups& gT, const Gro
   return out;
 }
 
+// the transpose application Z = Theta_c^T Y (the mirror image: environment^T, sandwich^T, boundary^T)
+std::vector<BlockTask> theta_t_tasks(const Groups& gA, const Groups& gT, const Groups& gU, const Groups& gTp,
+                                     const Groups& gL, const Groups& gR, const Groups& gD, const Q& q) {
+  std::vector<BlockTask> out;
+  // 1. H1[t, L, Dn] = EL[a, t, L] Y[a, Dn]: one a block (a = t + L) per output block
+  for (const Q& ct : gT.order) {
+    for (const Q& cl : gL.order) {
+      const Q ca = add(ct, cl), cd = sub(ca, q);
+      if (!gA.has(ca) || !gD.has(cd)) continue;
+      out.push_back({1, 1, {ct, cl, cd}, 2.0 * gA.n(ca) * gT.n(ct) * gL.n(cl) * gD.n(cd)});
+    }
+  }
+  // 2. H2[t, U, R] = C[L, U, R, Dn] H1[t, L, Dn], summed over the L blocks with Dn = L + U - R
+  for (const Q& ct : gT.order) {
+    for (const Q& cu : gU.order) {
+      const Q cr = add(sub(q, ct), cu);
+      if (!gR.has(cr)) continue;
+      BlockTask t{2, 0, {ct, cu, cr}, 0.0};
+      for (const Q& cl : gL.order) {
+        const Q cd = sub(add(cl, cu), cr);
+        if (!gD.has(cd)) continue;
+        ++t.terms;
+        t.flops += 2.0 * gT.n(ct) * gL.n(cl) * gU.n(cu) * gR.n(cr) * gD.n(cd);
+      }
+      if (t.terms) out.push_back(t);
+    }
+  }
+  // 3. Z[t', R] = T[t, U, t'] H2[t, U, R], summed over the U blocks with t = U + t'
+  for (const Q& ctp : gTp.order) {
+    const Q cr = sub(q, ctp);
+    if (!gR.has(cr)) continue;
+    BlockTask t{3, 0, {ctp, cr, {0, 0}}, 0.0};
+    for (const Q& cu : gU.order) {
+      const Q ct = add(cu, ctp);
+      if (!gT.has(ct)) continue;
+      ++t.terms;
+      t.flops += 2.0 * gT.n(ct) * gU.n(cu) * gTp.n(ctp) * gR.n(cr);
+    }
+    if (t.terms) out.push_back(t);
+  }
+  return out;
+}
+
 }  // namespace
 }  // namespace fpeps
 
-extern "C" fpeps_status fpeps_theta_block_tasks(const int32_t* qa, int32_t na, const int32_t* qt, int32_t nt,
+extern "C" fpeps_status fpeps_theta_block_tasks(int32_t op, const int32_t* qa, int32_t na, const int32_t* qt, int32_t nt,
                                                 const int32_t* qu, int32_t nu, const int32_t* qtp, int32_t ntp,
                                                 const int32_t* ql, int32_t nl, const int32_t* qr, int32_t nr,
                                                 const int32_t* qd, int32_t nd, const int32_t* q, int32_t* tasks,
                                                 double* flops, int32_t* n_inout) {
   if (!qa || !qt || !qu || !qtp || !ql || !qr || !qd || !q || !n_inout) return FPEPS_ERR_ARG;
+  if (op < 0 || op > 1) return FPEPS_ERR_ARG;
   if (na < 1 || nt < 1 || nu < 1 || ntp < 1 || nl < 1 || nr < 1 || nd < 1 || *n_inout < 0) return FPEPS_ERR_ARG;
   using namespace fpeps;
-  const std::vector<BlockTask> tab =
-      theta_tasks(groups_of(qa, na), groups_of(qt, nt), groups_of(qu, nu), groups_of(qtp, ntp), groups_of(ql, nl),
-                  groups_of(qr, nr), groups_of(qd, nd), Q{q[0], q[1]});
+  const Groups gA = groups_of(qa, na), gT = groups_of(qt, nt), gU = groups_of(qu, nu), gTp = groups_of(qtp, ntp),
+               gL = groups_of(ql, nl), gR = groups_of(qr, nr), gD = groups_of(qd, nd);
+  const std::vector<BlockTask> tab = op == 0 ? theta_tasks(gA, gT, gU, gTp, gL, gR, gD, Q{q[0], q[1]})
+                                             : theta_t_tasks(gA, gT, gU, gTp, gL, gR, gD, Q{q[0], q[1]});
   const int32_t cap = *n_inout;
   *n_inout = (int32_t)tab.size();
   if (!tasks || !flops) return cap == 0 ? FPEPS_OK : FPEPS_ERR_ARG;

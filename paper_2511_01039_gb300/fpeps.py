@@ -68,8 +68,8 @@ SIGNATURES = {
     "fpeps_import_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32, C.c_int32]),
     "fpeps_last_error": (C.c_char_p, [C.c_void_p]),
     "fpeps_env_select": (C.c_int, [C.c_void_p, C.c_int32]),
-    "fpeps_theta_block_tasks": (C.c_int, [C.c_void_p, C.c_int32] * 7 + [C.c_void_p, C.c_void_p, C.c_void_p,
-                                                                       C.POINTER(C.c_int32)]),
+    "fpeps_theta_block_tasks": (C.c_int, [C.c_int32] + [C.c_void_p, C.c_int32] * 7 +
+                                [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "fpeps_env_destroy": (None, [C.c_void_p]),
     "fpeps_boundary_shape": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32)]),
@@ -198,9 +198,9 @@ def fpeps_import_boundary(env, blob: bytes, next_row: int, layer: int):
     _check(env, lib().fpeps_import_boundary(env, buf, len(blob), next_row, layer))
 
 
-def fpeps_theta_block_tasks(qa, qt, qu, qtp, ql, qr, qd, q):
-    """Task table of the block-sparse Theta_c application to sector q (host only): a list of
-    (step, terms, output-block charges, flops per vector)."""
+def fpeps_theta_block_tasks(qa, qt, qu, qtp, ql, qr, qd, q, op=0):
+    """Task table of the block-sparse Theta_c (op 0) or Theta_c^T (op 1) application to sector q
+    (host only): a list of (step, terms, output-block charges, flops per vector)."""
     import numpy as np
     legs = [np.ascontiguousarray(np.asarray(x).reshape(-1, 2), dtype=np.int32) for x in (qa, qt, qu, qtp, ql, qr, qd)]
     qs = np.ascontiguousarray(np.asarray(q).reshape(2), dtype=np.int32)
@@ -208,10 +208,11 @@ def fpeps_theta_block_tasks(qa, qt, qu, qtp, ql, qr, qd, q):
     for x in legs:
         args += [x.ctypes.data, len(x)]
     n = C.c_int32(0)
-    _check(None, lib().fpeps_theta_block_tasks(*args, qs.ctypes.data, None, None, C.byref(n)))
+    _check(None, lib().fpeps_theta_block_tasks(op, *args, qs.ctypes.data, None, None, C.byref(n)))
     tab = np.zeros((max(n.value, 1), 8), dtype=np.int32)
     fl = np.zeros(max(n.value, 1))
-    _check(None, lib().fpeps_theta_block_tasks(*args, qs.ctypes.data, tab.ctypes.data, fl.ctypes.data, C.byref(n)))
+    _check(None, lib().fpeps_theta_block_tasks(op, *args, qs.ctypes.data, tab.ctypes.data, fl.ctypes.data,
+                                               C.byref(n)))
     out = []
     for i in range(n.value):
         step, terms = int(tab[i, 0]), int(tab[i, 1])

@@ -46,7 +46,24 @@ def test_task_table_arguments(fp):
     buf = np.zeros((1, 8), dtype=np.int32)
     fl = np.zeros(1)
     args = [p, 1] * 7
-    assert fp.lib().fpeps_theta_block_tasks(*args, p, buf.ctypes.data, fl.ctypes.data, ctypes.byref(n)) == 1
-    args[1] = 0
+    assert fp.lib().fpeps_theta_block_tasks(0, *args, p, buf.ctypes.data, fl.ctypes.data, ctypes.byref(n)) == 1
     n = ctypes.c_int32(0)
-    assert fp.lib().fpeps_theta_block_tasks(*args, p, None, None, ctypes.byref(n)) == 1
+    assert fp.lib().fpeps_theta_block_tasks(2, *args, p, None, None, ctypes.byref(n)) == 1   # unknown op
+    args[1] = 0
+    assert fp.lib().fpeps_theta_block_tasks(0, *args, p, None, None, ctypes.byref(n)) == 1
+
+
+@pytest.mark.parametrize("seed", [3, 5])
+def test_transpose_task_table_matches_the_oracle(fp, seed):
+    EL, qa, Tc, qt, qU, qtp, A, W, qsite, g = _setup(seed)
+    QL, _, QR, QD = qsite
+    sectors = sorted({tuple(x) for x in (qa[:, None, :] - QD[None, :, :]).reshape(-1, 2).tolist()})
+    k = 2
+    for q in sectors:
+        Y = g.standard_normal((len(qa), len(QD), k))
+        _, ref = BS.theta_t_blocks(EL, qa, Tc, qt, qU, qtp, A, W, qsite, Y, q)
+        got = fp.fpeps_theta_block_tasks(qa, qt, qU, qtp, QL, QR, QD, q, op=1)
+        assert len(got) == len(ref), q
+        for (step, terms, out, fl), t in zip(got, ref):
+            assert (step, terms, out) == (t.step, t.terms, tuple(t.out)), q
+            assert fl * k == pytest.approx(t.flops, rel=1e-12)

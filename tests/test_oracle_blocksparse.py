@@ -105,3 +105,26 @@ def test_planted_overwrite_instead_of_accumulate_is_caught(monkeypatch):
     monkeypatch.setattr(BS, "_accumulate", lambda acc, p: p)
     yb, _ = BS.theta_blocks(EL, qa, Tc, qt, qU, qtp, A, W, qsite, X, q)
     assert not np.allclose(yb, yd, atol=1e-12 * np.abs(yd).max())
+
+
+@pytest.mark.parametrize("seed", [3, 5])
+def test_transpose_block_application_equals_dense_for_every_sector(seed):
+    """Theta_c^T by charge blocks against the dense transpose application, every sector; its
+    tasks are disjoint per step, and <Y, Theta X> = <Theta^T Y, X> holds on the block results."""
+    EL, qa, Tc, qt, qU, qtp, A, W, qsite, g = _setup(seed)
+    QR, QD = qsite[2], qsite[3]
+    sectors = sorted({tuple(x) for x in (qa[:, None, :] - QD[None, :, :]).reshape(-1, 2).tolist()})
+    assert len(sectors) > 2
+    for q in sectors:
+        Y = g.standard_normal((len(qa), len(QD), 3)) * np.all(qa[:, None, :] - QD[None, :, :] == np.asarray(q),
+                                                              axis=-1)[:, :, None]
+        zd = B.theta_t(EL, Tc, A, W, Y)
+        zb, tasks = BS.theta_t_blocks(EL, qa, Tc, qt, qU, qtp, A, W, qsite, Y, q)
+        assert np.allclose(zb, zd, atol=1e-12 * max(1.0, np.abs(zd).max())), q
+        for step in (1, 2, 3):
+            keys = [t.out for t in tasks if t.step == step]
+            assert len(keys) == len(set(keys)), (q, step)
+        X = _sector_vectors(g, qtp, QR, q)
+        yb, _ = BS.theta_blocks(EL, qa, Tc, qt, qU, qtp, A, W, qsite, X, q)
+        lhs, rhs = float(np.sum(Y * yb)), float(np.sum(zb * X))
+        assert abs(lhs - rhs) <= 1e-10 * (1.0 + abs(lhs)), q
