@@ -228,9 +228,10 @@ fpeps_status fpeps_export_boundary(fpeps_env* env, void* host_buf, size_t* bytes
 fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t bytes, int32_t next_row,
                                    int32_t layer);
 
-/* Task table of the block-sparse application Y = Theta_c X (op 0) or
- * Z = Theta_c^T Y (op 1, the rSVD's transpose) to the vectors of one charge
- * sector q (Sec. III: contractions cut into quantum-number slices
+/* Task table of a block-sparse site map applied to the vectors of one charge
+ * sector q, the ops of fpeps_apply_theta_op: Y = Theta_c X (op 0), its
+ * transpose (op 1), the right-environment map of the CBE fit (op 2) and its
+ * transpose (op 3) (Sec. III: contractions cut into quantum-number slices
  * whose outputs do not overlap; Sec. IV: the application of the zip-up, pattern
  * 2(a)). Host code, no device work. With charge-conserving tensors each of the
  * three contractions (1: boundary x vectors, 2: the site sandwich, 3:
@@ -240,19 +241,23 @@ fpeps_status fpeps_import_boundary(fpeps_env* env, const void* host_buf, size_t 
  * left environment EL[a, t, L] q_a = q_t + Q_L; X[t', R] in sector q where
  * q_t' + Q_R = q, Y[a, Dn] where q_a - Q_Dn = q. Op 1 runs the mirror steps
  * (1: environment^T x vectors, 2: the sandwich transposed, 3: boundary^T x
- * vectors).
+ * vectors). For ops 2 and 3 the leg a is the right environment's bond,
+ * ER[a, t', R] with q_a = q_t' + Q_R, vectors X[Dn, a] with Q_Dn + q_a = q and
+ * Z[t, L] with q_t + Q_L = q.
  *   qa, qt, qu, qtp, ql, qr, qd  host int32 charge pairs of the legs a, t, U,
  *              t', L, R, Dn (n entries each, pairs interleaved); q the sector.
  *   tasks      host int32 [cap][8]: step (1..3), number of block products,
  *              then the output block's charges: op 0 step 1 (t, U, R), step 2
  *              (t, L, Dn), step 3 (a, Dn) and one zero pair; op 1 step 1
- *              (t, L, Dn), step 2 (t, U, R), step 3 (t', R) and one zero pair;
+ *              (t, L, Dn), step 2 (t, U, R), step 3 (t', R); op 2 step 1
+ *              (t', R, Dn), step 2 (t', L, U), step 3 (t, L); op 3 step 1
+ *              (t', L, U), step 2 (t', R, Dn), step 3 (Dn, a);
  *              steps in order, within a step the legs' charges in order of
  *              first appearance.
  *   flops      host double [cap]: 2 x multiply-adds of the task per vector.
  *   n_inout    in: cap; out: number of tasks. With cap 0 (tasks, flops may be
  *              NULL) only the count is returned.
- * Errors: FPEPS_ERR_ARG (op not 0 or 1, NULL pointer, empty leg, cap too
+ * Errors: FPEPS_ERR_ARG (op outside 0..3, NULL pointer, empty leg, cap too
  * small). */
 fpeps_status fpeps_theta_block_tasks(int32_t op, const int32_t* qa, int32_t na, const int32_t* qt, int32_t nt,
                                      const int32_t* qu, int32_t nu, const int32_t* qtp, int32_t ntp,

@@ -20,9 +20,10 @@ It restates, slowly and in double precision, what the GPU path computes:
                  sector-wise rSVD and one global truncation, and the CBE fit
                  with a sector-wise CBE rSVD and a sector-wise SVD of the
                  fitted tensor, on the dense applications of ``boundary``.
-* ``blocksparse`` - the site application Theta_c X by charge blocks (Sec. III
-                 quantum-number slices): one task per output block of each
-                 of its three contractions, with the task list.
+* ``blocksparse`` - the four site maps (Theta_c, its transpose, the fit's
+                 right-environment map and its transpose) by charge blocks
+                 (Sec. III quantum-number slices): one task per output block of
+                 each of their three contractions, with the task lists.
 
 It shares no code with the CUDA path; the only common module is the seeded
 input generator ``synth`` (data, no method arithmetic).

@@ -1,4 +1,5 @@
-// Task tables of the block-sparse site applications Y = Theta_c X and Z = Theta_c^T Y (host code).
+// Task tables of the block-sparse site maps (Theta_c, its transpose, the right-environment map of
+// the CBE fit and its transpose; host code).
 //
 // With charge-conserving tensors every contraction of the application (Sec. IV,
 // pattern 2(a) of Sec. III: boundary x vectors, the site sandwich, environment x
@@ -143,6 +144,93 @@ std::vector<BlockTask> theta_t_tasks(const Groups& gA, const Groups& gT, const G
   return out;
 }
 
+// the right-environment map of the CBE fit, Z[t, L] = ThetaR_c X[Dn, a] with ER[a, t', R]
+// (q_a = q_t' + Q_R; X in sector q: Q_Dn + q_a = q)
+std::vector<BlockTask> theta_r_tasks(const Groups& gA, const Groups& gT, const Groups& gU, const Groups& gTp,
+                                     const Groups& gL, const Groups& gR, const Groups& gD, const Q& q) {
+  std::vector<BlockTask> out;
+  // 1. W1[t', R, Dn] = ER[a, t', R] X[Dn, a]: one a block (a = t' + R) per output block
+  for (const Q& ctp : gTp.order) {
+    for (const Q& cr : gR.order) {
+      const Q ca = add(ctp, cr), cd = sub(q, ca);
+      if (!gA.has(ca) || !gD.has(cd)) continue;
+      out.push_back({1, 1, {ctp, cr, cd}, 2.0 * gA.n(ca) * gTp.n(ctp) * gR.n(cr) * gD.n(cd)});
+    }
+  }
+  // 2. W2[t', L, U] = C[L, U, R, Dn] W1[t', R, Dn], summed over the R blocks with Dn = L + U - R
+  for (const Q& ctp : gTp.order) {
+    for (const Q& cl : gL.order) {
+      const Q cu = sub(sub(q, ctp), cl);
+      if (!gU.has(cu)) continue;
+      BlockTask t{2, 0, {ctp, cl, cu}, 0.0};
+      for (const Q& cr : gR.order) {
+        const Q cd = sub(add(cl, cu), cr);
+        if (!gD.has(cd)) continue;
+        ++t.terms;
+        t.flops += 2.0 * gTp.n(ctp) * gL.n(cl) * gU.n(cu) * gR.n(cr) * gD.n(cd);
+      }
+      if (t.terms) out.push_back(t);
+    }
+  }
+  // 3. Z[t, L] = T[t, U, t'] W2[t', L, U], summed over the U blocks with t' = t - U
+  for (const Q& ct : gT.order) {
+    const Q cl = sub(q, ct);
+    if (!gL.has(cl)) continue;
+    BlockTask t{3, 0, {ct, cl, {0, 0}}, 0.0};
+    for (const Q& cu : gU.order) {
+      const Q ctp = sub(ct, cu);
+      if (!gTp.has(ctp)) continue;
+      ++t.terms;
+      t.flops += 2.0 * gT.n(ct) * gU.n(cu) * gTp.n(ctp) * gL.n(cl);
+    }
+    if (t.terms) out.push_back(t);
+  }
+  return out;
+}
+
+// its transpose, X[Dn, a] = ThetaR_c^T Z[t, L] (Z in sector q: q_t + Q_L = q)
+std::vector<BlockTask> theta_r_t_tasks(const Groups& gA, const Groups& gT, const Groups& gU, const Groups& gTp,
+                                       const Groups& gL, const Groups& gR, const Groups& gD, const Q& q) {
+  std::vector<BlockTask> out;
+  // 1. V1[t', L, U] = T[t, U, t'] Z[t, L]: one t block (t = U + t') per output block
+  for (const Q& ctp : gTp.order) {
+    for (const Q& cl : gL.order) {
+      const Q cu = sub(sub(q, ctp), cl), ct = add(cu, ctp);
+      if (!gU.has(cu) || !gT.has(ct)) continue;
+      out.push_back({1, 1, {ctp, cl, cu}, 2.0 * gT.n(ct) * gU.n(cu) * gTp.n(ctp) * gL.n(cl)});
+    }
+  }
+  // 2. V2[t', R, Dn] = C[L, U, R, Dn] V1[t', L, U], summed over the L blocks with U = R + Dn - L
+  for (const Q& ctp : gTp.order) {
+    for (const Q& cr : gR.order) {
+      const Q cd = sub(sub(q, ctp), cr);
+      if (!gD.has(cd)) continue;
+      BlockTask t{2, 0, {ctp, cr, cd}, 0.0};
+      for (const Q& cl : gL.order) {
+        const Q cu = sub(add(cr, cd), cl);
+        if (!gU.has(cu)) continue;
+        ++t.terms;
+        t.flops += 2.0 * gTp.n(ctp) * gL.n(cl) * gU.n(cu) * gR.n(cr) * gD.n(cd);
+      }
+      if (t.terms) out.push_back(t);
+    }
+  }
+  // 3. X[Dn, a] = ER[a, t', R] V2[t', R, Dn], summed over the t' blocks with R = a - t'
+  for (const Q& cd : gD.order) {
+    const Q ca = sub(q, cd);
+    if (!gA.has(ca)) continue;
+    BlockTask t{3, 0, {cd, ca, {0, 0}}, 0.0};
+    for (const Q& ctp : gTp.order) {
+      const Q cr = sub(ca, ctp);
+      if (!gR.has(cr)) continue;
+      ++t.terms;
+      t.flops += 2.0 * gA.n(ca) * gTp.n(ctp) * gR.n(cr) * gD.n(cd);
+    }
+    if (t.terms) out.push_back(t);
+  }
+  return out;
+}
+
 }  // namespace
 }  // namespace fpeps
 
@@ -152,13 +240,16 @@ extern "C" fpeps_status fpeps_theta_block_tasks(int32_t op, const int32_t* qa, i
                                                 const int32_t* qd, int32_t nd, const int32_t* q, int32_t* tasks,
                                                 double* flops, int32_t* n_inout) {
   if (!qa || !qt || !qu || !qtp || !ql || !qr || !qd || !q || !n_inout) return FPEPS_ERR_ARG;
-  if (op < 0 || op > 1) return FPEPS_ERR_ARG;
+  if (op < 0 || op > 3) return FPEPS_ERR_ARG;
   if (na < 1 || nt < 1 || nu < 1 || ntp < 1 || nl < 1 || nr < 1 || nd < 1 || *n_inout < 0) return FPEPS_ERR_ARG;
   using namespace fpeps;
   const Groups gA = groups_of(qa, na), gT = groups_of(qt, nt), gU = groups_of(qu, nu), gTp = groups_of(qtp, ntp),
                gL = groups_of(ql, nl), gR = groups_of(qr, nr), gD = groups_of(qd, nd);
-  const std::vector<BlockTask> tab = op == 0 ? theta_tasks(gA, gT, gU, gTp, gL, gR, gD, Q{q[0], q[1]})
-                                             : theta_t_tasks(gA, gT, gU, gTp, gL, gR, gD, Q{q[0], q[1]});
+  const Q qs{q[0], q[1]};
+  const std::vector<BlockTask> tab = op == 0   ? theta_tasks(gA, gT, gU, gTp, gL, gR, gD, qs)
+                                     : op == 1 ? theta_t_tasks(gA, gT, gU, gTp, gL, gR, gD, qs)
+                                     : op == 2 ? theta_r_tasks(gA, gT, gU, gTp, gL, gR, gD, qs)
+                                               : theta_r_t_tasks(gA, gT, gU, gTp, gL, gR, gD, qs);
   const int32_t cap = *n_inout;
   *n_inout = (int32_t)tab.size();
   if (!tasks || !flops) return cap == 0 ? FPEPS_OK : FPEPS_ERR_ARG;

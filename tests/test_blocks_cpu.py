@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import blocksparse as BS
-from test_oracle_blocksparse import _sector_vectors, _setup
+from test_oracle_blocksparse import _right_env, _sector_vectors, _setup
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def test_task_table_arguments(fp):
     args = [p, 1] * 7
     assert fp.lib().fpeps_theta_block_tasks(0, *args, p, buf.ctypes.data, fl.ctypes.data, ctypes.byref(n)) == 1
     n = ctypes.c_int32(0)
-    assert fp.lib().fpeps_theta_block_tasks(2, *args, p, None, None, ctypes.byref(n)) == 1   # unknown op
+    assert fp.lib().fpeps_theta_block_tasks(4, *args, p, None, None, ctypes.byref(n)) == 1   # unknown op
     args[1] = 0
     assert fp.lib().fpeps_theta_block_tasks(0, *args, p, None, None, ctypes.byref(n)) == 1
 
@@ -67,3 +67,21 @@ def test_transpose_task_table_matches_the_oracle(fp, seed):
         for (step, terms, out, fl), t in zip(got, ref):
             assert (step, terms, out) == (t.step, t.terms, tuple(t.out)), q
             assert fl * k == pytest.approx(t.flops, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", [3, 5])
+def test_right_environment_task_tables_match_the_oracle(fp, seed):
+    _, _, Tc, qt, qU, qtp, A, W, qsite, g = _setup(seed)
+    QL, _, QR, QD = qsite
+    ER, qa = _right_env(g, qtp, QR)
+    sectors = sorted({tuple(x) for x in (QD[:, None, :] + qa[None, :, :]).reshape(-1, 2).tolist()})
+    for q in sectors:
+        X = g.standard_normal((len(QD), len(qa), 1))
+        Z = g.standard_normal((len(qt), len(QL), 1))
+        for op, fn, v in ((2, BS.theta_r_blocks, X), (3, BS.theta_r_t_blocks, Z)):
+            _, ref = fn(ER, qa, Tc, qt, qU, qtp, A, W, qsite, v, q)
+            got = fp.fpeps_theta_block_tasks(qa, qt, qU, qtp, QL, QR, QD, q, op=op)
+            assert len(got) == len(ref), (op, q)
+            for (step, terms, out, fl), t in zip(got, ref):
+                assert (step, terms, out) == (t.step, t.terms, tuple(t.out)), (op, q)
+                assert fl == pytest.approx(t.flops, rel=1e-12)

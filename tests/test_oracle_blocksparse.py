@@ -128,3 +128,40 @@ def test_transpose_block_application_equals_dense_for_every_sector(seed):
         yb, _ = BS.theta_blocks(EL, qa, Tc, qt, qU, qtp, A, W, qsite, X, q)
         lhs, rhs = float(np.sum(Y * yb)), float(np.sum(zb * X))
         assert abs(lhs - rhs) <= 1e-10 * (1.0 + abs(lhs)), q
+
+
+def _right_env(g, qtp, QR, n=12):
+    """A random right environment ER[a, t', R] with q_a = q_t' + Q_R."""
+    reach = sorted({tuple(x) for x in (qtp[:, None, :] + QR[None, :, :]).reshape(-1, 2).tolist()})
+    qa = np.array([reach[i] for i in g.integers(0, len(reach), n)], dtype=np.int64)
+    ER = g.standard_normal((n, len(qtp), len(QR)))
+    ok = np.all(qa[:, None, None, :] == qtp[None, :, None, :] + QR[None, None, :, :], axis=-1)
+    return ER * ok, qa
+
+
+@pytest.mark.parametrize("seed", [3, 5])
+def test_right_environment_maps_by_blocks_equal_dense(seed):
+    """ThetaR_c and its transpose by charge blocks against the dense maps, every sector, with
+    disjoint tasks per step and the adjoint identity <Z, ThetaR X> = <ThetaR^T Z, X>."""
+    _, _, Tc, qt, qU, qtp, A, W, qsite, g = _setup(seed)
+    QL, _, QR, QD = qsite
+    ER, qa = _right_env(g, qtp, QR)
+    sectors = sorted({tuple(x) for x in (QD[:, None, :] + qa[None, :, :]).reshape(-1, 2).tolist()})
+    assert len(sectors) > 2
+    for q in sectors:
+        X = g.standard_normal((len(QD), len(qa), 2)) * np.all(QD[:, None, :] + qa[None, :, :] == np.asarray(q),
+                                                              axis=-1)[:, :, None]
+        zd = B.theta_r(ER, Tc, A, W, X)
+        zb, tasks = BS.theta_r_blocks(ER, qa, Tc, qt, qU, qtp, A, W, qsite, X, q)
+        assert np.allclose(zb, zd, atol=1e-12 * max(1.0, np.abs(zd).max())), q
+        Zin = g.standard_normal((len(qt), len(QL), 2)) * np.all(qt[:, None, :] + QL[None, :, :] == np.asarray(q),
+                                                                axis=-1)[:, :, None]
+        xd = B.theta_r_t(ER, Tc, A, W, Zin)
+        xb, tasks_t = BS.theta_r_t_blocks(ER, qa, Tc, qt, qU, qtp, A, W, qsite, Zin, q)
+        assert np.allclose(xb, xd, atol=1e-12 * max(1.0, np.abs(xd).max())), q
+        for tl in (tasks, tasks_t):
+            for step in (1, 2, 3):
+                keys = [t.out for t in tl if t.step == step]
+                assert len(keys) == len(set(keys)), (q, step)
+        lhs, rhs = float(np.sum(Zin * zb)), float(np.sum(xb * X))
+        assert abs(lhs - rhs) <= 1e-10 * (1.0 + abs(lhs)), q
